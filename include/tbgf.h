@@ -1,0 +1,210 @@
+/*
+ * tbgf: GB300 (sm_103a) library for the generalized shifted linear equations
+ *
+ *     (z S - H) x = b                                  (Eq. 2, Sec. 3)
+ *
+ * for many complex energies z and unit right-hand sides b = e_j, solved by a
+ * shifted COCG (the first solver named in Sec. 3), and for the reduction of
+ * the resulting Green's-function entries G_ij(z) = e_i^T (z S - H)^{-1} e_j to
+ * local densities of states and density-matrix elements (the Green's-function
+ * based quantities of Sec. 2).  H and S are the sparse real-symmetric
+ * Hamiltonian and overlap of an atom-orbital (LCAO) basis, S positive definite
+ * with unit diagonal (Sec. 2 Eq. 1, Sec. 8).
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only.  Complex numbers are two doubles (re, im), arrays of
+ *    them are interleaved, row-major.
+ *  - Array arguments are owned by the caller.  Unless an entry point says
+ *    otherwise each array may live in host memory or in device memory of the
+ *    current CUDA device; the library detects which (cudaPointerGetAttributes)
+ *    and stages host arrays through its own device buffers, copying host
+ *    outputs back before it returns.
+ *  - Work is queued on the CUDA stream passed in (NULL = legacy default
+ *    stream).  With device-resident outputs an entry point may return before
+ *    the work finishes; synchronise the stream before reading them.  With any
+ *    host-resident output it synchronises before returning.
+ *  - Indices are 0-based.  Row indices are int64, block-column indices int32.
+ *  - Every entry point returns an int status: 0 = success, negative = error
+ *    (nothing useful was written), positive = warnings (bit mask, see below).
+ *    Nothing throws across the boundary.  tb_status_string() names a status.
+ */
+#ifndef TBGF_H
+#define TBGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define TB_OK 0
+#define TB_ERR_ARG (-1)         /* an argument is invalid                           */
+#define TB_ERR_CUDA (-2)        /* a CUDA call failed (see tb_last_error)           */
+#define TB_ERR_ALLOC (-3)       /* device or host allocation failed                 */
+#define TB_ERR_UNSUPPORTED (-4) /* a valid request this build does not implement    */
+#define TB_ERR_SIZE (-5)        /* a size exceeds an internal limit                 */
+#define TB_ERR_STRUCTURE (-6)   /* a matrix structure is malformed                  */
+
+/* positive return values of shifted_cocg_solve: OR of these over columns */
+#define TB_WARN_MAX_ITER 1
+#define TB_WARN_BREAKDOWN 2
+#define TB_WARN_NONFINITE 4
+
+/* per-column status written by shifted_cocg_solve */
+#define TB_COL_CONVERGED 0 /* every shift met the tolerance                     */
+#define TB_COL_MAX_ITER 1  /* max_iter reached with some shift above tolerance  */
+#define TB_COL_BREAKDOWN 2 /* rho_n = r^T S r or mu_n = p^T (z_s S - H) p is 0  */
+#define TB_COL_NONFINITE 3 /* a recurrence scalar became inf or NaN             */
+
+/* ------------------------------------------------------------- context */
+typedef struct tb_ctx tb_ctx;
+
+/* Create a context bound to the current CUDA device.  It owns the library's
+ * device workspace (grown on demand, freed by tb_ctx_destroy).  One context
+ * must not be used from two host threads at once. */
+int tb_ctx_create(tb_ctx **out);
+int tb_ctx_destroy(tb_ctx *ctx);
+const char *tb_status_string(int status);
+/* The message of the last failure recorded in ctx (never NULL). */
+const char *tb_last_error(const tb_ctx *ctx);
+/* Library version, e.g. 10000 for 1.0.0. */
+int tb_version(void);
+
+/* ------------------------------------------------------ system builder */
+/* Synthetic tight-binding systems with the structure Sec. 8 states for the
+ * LCAO matrices: H, S real symmetric, S_ii = 1, |S_ij| < 1, S positive
+ * definite (checked by Gershgorin dominance), nearest-neighbour sparsity.   */
+#define TB_LATTICE_SC_PERIODIC 0 /* L^3 simple cubic, periodic, 6 NN; L >= 3    */
+#define TB_LATTICE_FCC_CLUSTER 1 /* n_sites FCC sites nearest the origin, open  */
+
+#define TB_ONSITE_UNIFORM 0     /* u * I, u ~ U[onsite_lo, onsite_hi] per atom       */
+#define TB_ONSITE_DIAG_NORMAL 1 /* diag(onsite_diag) + (N + N^T)/2, N ~ N(0,sigma)   */
+#define TB_HOP_CONST 0          /* hop_t * I on every NN pair                        */
+#define TB_HOP_NORMAL 1         /* X ~ N(0, hop_sigma) per pair, X_ji = X_ij^T       */
+#define TB_S_IDENTITY 0         /* S = I (no S matrix is produced)                   */
+#define TB_S_NORMAL 1           /* S = I + symmetric NN blocks N(0, s_param)         */
+#define TB_S_CONST 2            /* S = I + s_param * I on every NN pair              */
+
+typedef struct {
+    int32_t lattice;
+    int32_t L;              /* SC edge length                                      */
+    int64_t n_sites;        /* FCC: sites kept before vacancies and slab           */
+    int32_t bdim;           /* orbitals per atom = block edge, 1..16               */
+    int32_t onsite_mode;
+    double onsite_lo, onsite_hi, onsite_sigma;
+    double onsite_diag[16];
+    int32_t hop_mode;
+    double hop_t, hop_sigma;
+    int32_t s_mode;
+    double s_param;
+    double vacancy_frac;    /* FCC only: fraction of sites removed                 */
+    int32_t slab;           /* FCC only: remove sites above a random z cut         */
+    double subst_frac;      /* fraction of atoms whose onsite block gets + shift*I */
+    double subst_shift;
+} tb_system_spec;
+
+/* Block-sparse row matrix with bdim x bdim blocks.
+ *   row_ptr int64[n_brows+1], col_idx int32[nnzb] ascending within each block
+ *   row with the diagonal block present, val double[nnzb*bdim*bdim] with each
+ *   block row-major.  bdim = 1 is plain CSR. */
+typedef struct {
+    int64_t n_brows;
+    int32_t bdim;
+    int64_t nnzb;
+    int64_t *row_ptr;
+    int32_t *col_idx;
+    double *val;
+} tb_bsr;
+
+/* Build H (and S unless s_mode is TB_S_IDENTITY) for `spec` from `seed`.
+ * Host memory only.  Two phases: with H->row_ptr == NULL only n_brows, bdim
+ * and nnzb of H (and S) are filled; then call again with row_ptr, col_idx and
+ * val allocated to those sizes.  S may be NULL when s_mode is TB_S_IDENTITY.
+ * Random values come from Philox4x32-10 keyed by the seed, counter
+ * (index, stream); *overlap_seed (optional) receives the seed the overlap
+ * draws used (seed + k when the first k draws failed the dominance check).
+ * Integer structure is a deterministic function of spec (bit-exact).
+ * Errors: TB_ERR_ARG for an invalid spec (e.g. L < 3), TB_ERR_SIZE when
+ * the structure does not fit int32 block-column indices. */
+int tb_build_bsr(const tb_system_spec *spec, uint64_t seed, tb_bsr *H, tb_bsr *S,
+                 uint64_t *overlap_seed);
+/* tb_build_bsr for bdim = 1 (scalar CSR); TB_ERR_ARG if spec->bdim != 1. */
+int tb_build_csr(const tb_system_spec *spec, uint64_t seed, tb_bsr *H, tb_bsr *S,
+                 uint64_t *overlap_seed);
+
+/* ---------------------------------------------------------- sparse product */
+#define TB_PREC_FP64 0  /* all vectors and arithmetic in FP64                      */
+#define TB_PREC_MIXED 1 /* FP32 vectors, SpMM and updates with FP32 accumulation;
+                           FP64 recurrence scalars, dot products, convergence
+                           tests, projected solutions and reductions           */
+
+/* Y = A X for a real BSR matrix A (n = n_brows*bdim rows) and a complex panel
+ * X of ncols columns: X, Y complex double [n][ncols] (row-major, interleaved).
+ * precision TB_PREC_MIXED rounds A and X to FP32 and accumulates in FP32.
+ * ncols in {1..64}.  The sparse product shared by every shift in each COCG
+ * iteration (Sec. 3); exposed for measurement and tests. */
+int tb_bsr_spmm(tb_ctx *ctx, const tb_bsr *A, const double *X, int32_t ncols, double *Y,
+                int32_t precision, void *stream);
+
+/* ------------------------------------------------------ shifted COCG solve */
+typedef struct {
+    double tol;          /* stop a shift when ||b - (zS-H)x|| <= tol ||b|| (recurrence
+                            residual), default 1e-10                              */
+    int32_t max_iter;    /* outer iterations, default 100000                        */
+    int32_t precision;   /* TB_PREC_FP64 (default) or TB_PREC_MIXED               */
+    int32_t panel_w;     /* columns solved together; 0 = autotuned                */
+    int32_t seed_shift;  /* index of the seed shift; -1 = median Re z (default)    */
+    double inner_tol;    /* S != I: relative tolerance of the inner CG on S;
+                            0 = default (1e-13 FP64, 1e-7 mixed)                  */
+    int32_t inner_max;   /* S != I: inner iterations per outer iteration, 0 = 40   */
+    int32_t reserved0;
+    void *stream;        /* cudaStream_t to queue work on                         */
+} tb_solve_opts;
+
+/* Fill `opts` with the defaults above. */
+void tb_solve_opts_default(tb_solve_opts *opts);
+
+/* Solve (z_m S - H) x = e_j for every shift z_m (m < n_z) and every column
+ * j = rhs_rows[c] (c < n_rhs), keeping x on the rows asked for:
+ *
+ *   G[(out_row_ptr[c] + k) * n_z + m] = e_i^T (z_m S - H)^{-1} e_j,
+ *       i = out_rows[out_row_ptr[c] + k],  0 <= k < out_row_ptr[c+1]-out_row_ptr[c]
+ *
+ * H and S (S = NULL means S = I) are BSR with the same bdim and n_brows, their
+ * arrays in device memory or host memory (staged).  z: complex [n_z].
+ * Outputs: G complex [out_row_ptr[n_rhs]][n_z]; iters int32[n_rhs] (outer
+ * iterations run); resid double[n_rhs][n_z] (final recurrence residual
+ * ||rt_n|| / |pi^m_n| relative to ||b||); status int32[n_rhs] (TB_COL_*).
+ * Method: one seed COCG per column in the S-bilinear form with the shifted
+ * systems following through collinear residuals (Sec. 3; recurrences in the
+ * library's design notes), columns batched into panels so that one block
+ * sparse product per iteration serves every column and every shift.
+ * Returns TB_OK, or a positive OR of TB_WARN_* when some column did not
+ * converge, or a negative error. */
+int shifted_cocg_solve(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z,
+                       int32_t n_z, const int64_t *rhs_rows, int64_t n_rhs,
+                       const int64_t *out_row_ptr, const int64_t *out_rows,
+                       const tb_solve_opts *opts, double *G, int32_t *iters, double *resid,
+                       int32_t *status);
+
+/* ----------------------------------------------- Green's function -> LDOS, DM */
+/* From the output of shifted_cocg_solve (same rhs/out-row layout):
+ *   ldos[c*n_z + m] = -(1/pi) Im sum_k G_{i_k j}(z_m) S_{i_k j}   (Mulliken form;
+ *                     S = NULL: -(1/pi) Im G_jj(z_m), row j must be kept)
+ *   dm[out_row_ptr[c] + k] = -(1/pi) Im sum_m w[m] f(Re z_m) G_{i_k j}(z_m)
+ * with f the Fermi-Dirac occupation at (mu, kT), kT = 0 a step with
+ * f(mu) = 1/2, and w the quadrature weights (double[n_z]).  Either of ldos and
+ * dm may be NULL.  All reductions in FP64.  Sec. 2 (DOS and Green's-function
+ * analysis); the formulas are the standard ones, the paper prints none.
+ * Errors: TB_ERR_ARG when S = NULL and a column does not keep its own row. */
+int gf_reduce_ldos_dm(tb_ctx *ctx, const double *G, int32_t n_z, const double *z,
+                      const double *w, double mu, double kT, const int64_t *rhs_rows,
+                      int64_t n_rhs, const int64_t *out_row_ptr, const int64_t *out_rows,
+                      const tb_bsr *S, double *ldos, double *dm, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TBGF_H */
