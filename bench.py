@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark: shift-RHS solves/s of the shifted-COCG Green's-function solve.
+
+Workload: the generalized (S != I) sp3-like system on a 32^3 periodic simple
+cubic lattice (M = 131072, 4x4 blocks), 64 shifts E + 0.005i on [-10, 6], the
+4096 right-hand sides e_j of orbital 0 of the atoms of the 16^3 sub-block,
+tolerance 1e-5 on the relative residual of every shift.  One step solves one
+panel of right-hand sides to convergence (every shift of every column) and
+reduces the Green's-function entries to LDOS and density-matrix elements.
+value = converged (column, shift) pairs / second over all ranks, inputs
+resident in HBM; e2e = the same through the C ABI with host buffers (pinned),
+copies included.  Multi-GPU: ranks take disjoint panels (weak scaling); there
+is no collective in the data path.
+
+--impl reference times the CPU oracle (plain FP64 shifted COCG, OpenMP over
+columns) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "shift-RHS solves/s at rel. residual 1e-5 (mixed+batched vs plain FP64); SpMM HBM GB/s"
+UNIT = "shift-RHS solves/s"
+WORKLOAD = wl.C2
+
+
+def workload_config(panel_w: int, precision: str, n_gpus: int) -> dict:
+    s = WORKLOAD.system
+    return {
+        "workload": f"{WORKLOAD.name}: SC {s.L}^3 periodic, 4 orbitals/atom (M={s.L ** 3 * s.bdim}), "
+                    f"S=I+NN N(0,{s.s_param}), {WORKLOAD.n_shifts} shifts E+{WORKLOAD.eta}i on "
+                    f"[{WORKLOAD.e_lo},{WORKLOAD.e_hi}], {WORKLOAD.n_rhs} RHS (orbital 0 of the 16^3 sub-block)",
+        "tol": WORKLOAD.tol,
+        "rhs_per_step_per_gpu": panel_w,
+        "panel_w": panel_w,
+        "precision": precision,
+        "parallelism": f"column shards x{n_gpus}",
+        "l2": "inputs larger than L2 (panel vectors alone exceed 129 MB)",
+    }
+
+
+def block_pattern_rows(row_ptr, col_idx, bdim, rows):
+    """Kept rows of each column: every orbital of the atoms in its block pattern."""
+    out = []
+    for j in rows:
+        a = j // bdim
+        cols = col_idx[row_ptr[a]:row_ptr[a + 1]].astype(np.int64)
+        out.append((cols[:, None] * bdim + np.arange(bdim)[None, :]).ravel())
+    ptr = np.zeros(len(out) + 1, np.int64)
+    ptr[1:] = np.cumsum([len(o) for o in out])
+    return ptr, np.concatenate(out).astype(np.int64)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        if shutil.which("nvidia-smi"):
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_traffic(kernel: str) -> int | None:
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "solver_kernels_c2_mixed_w64.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    src = open(os.path.join(ROOT, "paper_1402_7285_gb300", "csrc", "cocg.cu"), "rb").read()
+    if not m or m.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    m = re.search(rf"traffic_bytes_per_launch\s+{re.escape(kernel)}\s*=\s*([0-9]+)", text)
+    return int(m.group(1)) if m else None
+
+
+def algorithmic_bytes(n_rows, nnzb, bdim, n_brows, W, n_z, n_ent, esz):
+    """Bytes each solver kernel must move once per launch (matrix read once, panel vectors once)."""
+    V = n_rows * W * 2 * esz                     # one complex panel vector
+    Mb = nnzb * bdim * bdim * esz + nnzb * 4 + (n_brows + 1) * 8
+    proj = n_ent * n_z * 16                      # one FP64 complex projected-state array
+    return {
+        "A_outer_H_product": 7 * V + Mb + 2 * proj,     # R, P_old, RT, SP in; P, SP, U out; p^m rw
+        "B_update": 6 * V + Mb + 3 * proj,              # RT, U, R in; RT, R', T out; S; x^m rw, p^m in
+        "IC_A_inner_S_product": 4 * V + Mb,             # T, D_old in; D, A out; S
+        "IC_B_inner_update": 6 * V,                     # Y, D, T, A in; Y, T out
+        "C_rho": 2 * V,                                 # R, RT in
+    }
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1402_7285_gb300 as tb
+
+    dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
+    torch.cuda.set_device(dev)
+    prec = tb.TB_PREC_MIXED if args.precision == "mixed" else tb.TB_PREC_FP64
+    W = args.panel_w
+    Hh, Sh, _ = tb.build_system(WORKLOAD.system, WORKLOAD.seed)
+    H, S = Hh.to(dev), Sh.to(dev)
+    z = wl.shifts_of(WORKLOAD)
+    rows_all = wl.rhs_of(WORKLOAD)
+    n_z = len(z)
+    E = z.real
+    w_q = np.full(n_z, (WORKLOAD.e_hi - WORKLOAD.e_lo) / n_z)
+    mu, kT = -2.0, 0.0
+    n_panels_total = len(rows_all) // W
+
+    def panel(step):
+        k = (step * world + rank) % n_panels_total
+        cols = rows_all[k * W:(k + 1) * W]
+        ptr, orows = block_pattern_rows(Hh.row_ptr, Hh.col_idx, Hh.bdim, cols)
+        return cols, ptr, orows
+
+    def dev_panel(step):
+        cols, ptr, orows = panel(step)
+        return (torch.as_tensor(cols, device=dev), torch.as_tensor(ptr, device=dev),
+                torch.as_tensor(orows, device=dev))
+
+    ctx = tb.Context()
+    zt = torch.as_tensor(z, device=dev)
+    wt = torch.as_tensor(w_q, device=dev)
+
+    def step_device(cols, ptr, orows):
+        r = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=prec, panel_w=W)
+        L, D = tb.reduce_ldos_dm(ctx, r.G, zt, wt, mu, kT, cols, ptr, orows, S=S)
+        return r
+
+    def converged_pairs(r):
+        res = r.resid.cpu().numpy() if hasattr(r.resid, "cpu") else r.resid
+        return int((res <= WORKLOAD.tol).sum())
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    panels = [dev_panel(s) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        step_device(*panels[s])
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for s in range(args.warmup, args.warmup + args.steps):
+            results.append(step_device(*panels[s]))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    pairs = sum(converged_pairs(r) for r in results)
+    outer = sum(r.outer_iters for r in results)
+    inner = sum(r.inner_iters for r in results)
+    launches = sum(13 + 3 * r.outer_iters + 2 * r.inner_iters for r in results)
+    t = torch.tensor([ms, pairs, launches], dtype=torch.float64, device=dev)
+    if world > 1:
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        ms_max, pairs_all, launches_all = float(mx[0]), float(sm[1]), float(sm[2])
+    else:
+        ms_max, pairs_all, launches_all = ms, float(pairs), float(launches)
+    value = pairs_all / (ms_max / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        Hp = tb.Bsr(Hh.n_brows, Hh.bdim, pin(Hh.row_ptr), pin(Hh.col_idx), pin(Hh.val))
+        Sp = tb.Bsr(Sh.n_brows, Sh.bdim, pin(Sh.row_ptr), pin(Sh.col_idx), pin(Sh.val))
+        zp = pin(z)
+        wp = pin(w_q)
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        host_panels = [tuple(pin(a) for a in panel(args.warmup + s)) for s in range(e2e_steps)]
+        h2d = sum(int(a.numel() * a.element_size()) for a in (Hp.row_ptr, Hp.col_idx, Hp.val, Sp.row_ptr,
+                                                             Sp.col_idx, Sp.val, zp, wp))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_pairs, h2d_b, d2h_b = 0, 0, 0
+        for cols, ptr, orows in host_panels:
+            r = tb.solve(ctx, Hp, Sp, zp, cols, ptr, orows, tol=WORKLOAD.tol, precision=prec, panel_w=W)
+            L, D = tb.reduce_ldos_dm(ctx, r.G, zp, wp, mu, kT, cols, ptr, orows, S=Sp)
+            e2e_pairs += int((r.resid <= WORKLOAD.tol).sum())
+            h2d_b += h2d + sum(int(a.numel() * a.element_size()) for a in (cols, ptr, orows)) * 2
+            d2h_b += r.G.nbytes + r.iters.nbytes + r.resid.nbytes + r.status.nbytes + L.nbytes + D.nbytes
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        tt = torch.tensor([e2e_s, e2e_pairs], dtype=torch.float64, device=dev)
+        if world > 1:
+            mx = tt.clone()
+            torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+            sm = tt.clone()
+            torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+            e2e_s, e2e_pairs = float(mx[0]), float(sm[1])
+        e2e = {"value": e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d_b // e2e_steps,
+               "d2h_bytes_per_step": d2h_b // e2e_steps, "steps": e2e_steps}
+
+    # ---- roofline of the dominant kernel (CUDA events on this stream)
+    cols, ptr, orows = panels[0]
+    prof = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W)
+    counts = {"A_outer_H_product": outer, "B_update": outer, "IC_A_inner_S_product": inner,
+              "IC_B_inner_update": inner, "C_rho": outer}
+    share = {k: prof[k] * counts[k] for k in prof}
+    dom = max(share, key=share.get)
+    n_ent = int(ptr[-1].item())
+    esz = 4 if prec == tb.TB_PREC_MIXED else 8
+    algo = algorithmic_bytes(Hh.n_rows, Hh.nnzb, Hh.bdim, Hh.n_brows, W, n_z, n_ent, esz)
+    peaks = measured_peaks()
+    achieved = algo[dom] / (prof[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm" if prec == tb.TB_PREC_MIXED else "alu", "kernel": dom, "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "traffic": kernel_traffic(dom), "peak_source": peaks["source"] + " (burst, kernel timed alone)",
+            "bytes_per_launch": algo[dom], "ms_per_launch": prof[dom],
+            "per_kernel_ms": prof, "per_kernel_share": {k: share[k] / sum(share.values()) for k in share},
+            "per_kernel_gbs": {k: algo[k] / (prof[k] * 1e-3) / 1e9 for k in prof if prof[k] > 0}}
+    ctx.close()
+    return {"value": value, "ms": ms_max, "pairs": pairs_all, "launches": launches_all, "clocks": clk.summary(),
+            "e2e": e2e, "roofline": roof, "outer_iters": outer, "inner_iters": inner,
+            "iters_per_column": [int(x) for r in results for x in (r.iters.cpu().numpy() if hasattr(r.iters, "cpu")
+                                                                    else r.iters)]}
+
+
+def cpu_oracle_sample(target_seconds: float, iters_needed: float | None):
+    """The oracle (plain FP64 shifted COCG, C + OpenMP over columns) on a bounded sample.
+
+    Runs `cores` columns of the workload for a fixed number of outer
+    iterations, measures seconds per outer iteration per column, and scales to
+    shift-RHS solves/s with `iters_needed` outer iterations per column."""
+    from oracle import cocg, systems
+
+    cores = os.cpu_count() or 1
+    s = systems.build_system(WORKLOAD.system, WORKLOAD.seed)
+    hc, sc = s.H.to_csr(), s.S.to_csr()
+    z = wl.shifts_of(WORKLOAD)
+    rows = wl.rhs_of(WORKLOAD)[:cores]
+    rl = [systems.block_pattern_rows(s.H, j) for j in rows]
+    ptr = np.zeros(len(rl) + 1, np.int64)
+    ptr[1:] = np.cumsum([len(r) for r in rl])
+    orows = np.concatenate(rl)
+    # calibrate: 2 iterations, then size the sample to target_seconds
+    t0 = time.perf_counter()
+    cocg.shifted_cocg(hc, sc, z, rows, ptr, orows, tol=WORKLOAD.tol, max_iter=2, inner_tol=1e-8, nthreads=cores)
+    per_iter = (time.perf_counter() - t0) / 2
+    k = int(max(2, min(2000, target_seconds / max(per_iter, 1e-6))))
+    t0 = time.perf_counter()
+    cocg.shifted_cocg(hc, sc, z, rows, ptr, orows, tol=WORKLOAD.tol, max_iter=k, inner_tol=1e-8, nthreads=cores)
+    dt = time.perf_counter() - t0
+    sec_per_iter = dt / k           # for `cores` columns in parallel
+    need = iters_needed or 20000.0
+    value = len(rows) * len(z) / (sec_per_iter * need)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(rows)} columns x {k} outer iterations of plain FP64 shifted COCG (inner CG tol 1e-8), "
+                      f"{dt:.1f} s; scaled to {need:.0f} outer iterations per column"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--panel-w", type=int, default=64)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--profile-reps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        samples = []
+        for _ in range(args.warmup):
+            cpu_oracle_sample(max(1.0, args.cpu_seconds / 4), None)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = cpu_oracle_sample(args.cpu_seconds / max(1, args.steps), None)
+            vals.append(r["value"])
+            samples.append(r)
+        dt = time.perf_counter() - t0
+        v = float(np.median(vals))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload_config(args.panel_w, "fp64 (oracle)", args.gpus),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": samples[-1]["cores"], "kind": "oracle",
+                                 "sample": samples[-1]["sample"]},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "gpu_launches": 0}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        iters = np.mean(out["iters_per_column"]) if out["iters_per_column"] else None
+        cpu = cpu_oracle_sample(args.cpu_seconds, iters)
+    line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic", "config": workload_config(args.panel_w, args.precision, args.gpus),
+            "clocks": out["clocks"], "e2e": out["e2e"], "gpu_launches": int(out["launches"]),
+            "roofline": out["roofline"], "cpu_baseline": cpu,
+            "solver": {"outer_iters": out["outer_iters"], "inner_iters": out["inner_iters"],
+                       "mean_iters_per_column": float(np.mean(out["iters_per_column"]))}}
+    print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

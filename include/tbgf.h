@@ -161,6 +161,8 @@ typedef struct {
     int32_t inner_max;   /* S != I: inner iterations per outer iteration, 0 = 40   */
     int32_t reserved0;
     void *stream;        /* cudaStream_t to queue work on                         */
+    int64_t *stats;      /* optional host array [2]: outer and inner iterations
+                            summed over all panels (written before returning)     */
 } tb_solve_opts;
 
 /* Fill `opts` with the defaults above. */
@@ -188,6 +190,20 @@ int shifted_cocg_solve(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const doub
                        const int64_t *out_row_ptr, const int64_t *out_rows,
                        const tb_solve_opts *opts, double *G, int32_t *iters, double *resid,
                        int32_t *status);
+
+/* Times the kernels of one solver iteration (the Sec. 3 step sequence) for
+ * the first panel of the given problem (same arguments and options as
+ * shifted_cocg_solve, no outputs).  After the panel is initialised, the
+ * sequence  A, B, [IC_A, IC_B], C  (the bracketed pair and C only when
+ * S != NULL) is launched `reps` times as ordinary launches on opts->stream,
+ * each kernel bracketed by CUDA events.  ms[k] (k < 8) receives the average
+ * milliseconds per launch of kernel k: 0 A (H product, shifted steps),
+ * 1 B (residual update; with S also the S product of the inner start),
+ * 2 IC_A (S product of the inner CG), 3 IC_B (inner CG update), 4 C (rho);
+ * unused entries are 0.  These are the kernels the solve's graph runs. */
+int shifted_cocg_profile(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, int32_t n_z,
+                         const int64_t *rhs_rows, int64_t n_rhs, const int64_t *out_row_ptr,
+                         const int64_t *out_rows, const tb_solve_opts *opts, int32_t reps, double *ms);
 
 /* ----------------------------------------------- Green's function -> LDOS, DM */
 /* From the output of shifted_cocg_solve (same rhs/out-row layout):

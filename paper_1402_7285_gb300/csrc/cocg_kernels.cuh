@@ -1,0 +1,238 @@
+// Kernels of the panel shifted-COCG solver (generalized shifted COCG, Sec. 3, Eq. 2).
+//
+// A panel holds W right-hand sides e_j ("slots"), each its own seed COCG in the
+// S-bilinear form <u, v> = u^T S v with the same seed shift z_s; the shifted
+// systems follow through the collinear residuals r^m = r / pi^m.  Per outer
+// iteration n (restated from the shifted-Krylov mathematics; rt = S r is the
+// residual of the original equation):
+//   A : p_n = r_n + beta_{n-1} p_{n-1};  Sp_n = rt_n + beta_{n-1} Sp_{n-1};
+//       u = z_s Sp_n - H p_n;  mu_n = p_n^T u;        (one BSR product with H)
+//       per (slot, shift): pi rotation, residual test, p^m_n on the kept rows;
+//       last CTA: alpha_n = rho_n / mu_n, column done/breakdown, panel done.
+//   B : (S = I) rt_{n+1} = rt_n - alpha_n u; rho_{n+1} = rt^T rt; ||rt||^2;
+//       per (slot, shift): pi_{n+1}, alpha^m_n, x^m += alpha^m_n p^m_n;
+//       last CTA: beta_n, iteration count, loop condition.
+//   B': (S != I) rt_{n+1} = rt_n - alpha_n u; y_0 = r_n - alpha_n u;
+//       t_0 = rt_{n+1} - S y_0 (one BSR product with S); shifted updates as B;
+//       then the inner CG on S: IC_A (d = t + b d, a = S d, d^H a) and
+//       IC_B (y += a d, t -= a a, t^H t), repeated in a device-side loop;
+//   C : rho_{n+1} = r_{n+1}^T rt_{n+1}; last CTA as in B.
+// All recurrence scalars are FP64.  The loop runs as CUDA-graph conditional
+// WHILE nodes whose conditions the last CTA of B / C / IC_B sets; every loop
+// has a hard iteration cap, so the device loop always ends.
+#pragma once
+
+#include "common.cuh"
+#include "spmm.cuh"
+
+namespace tbgf {
+
+struct ColState {
+    c64 rho;        // rho_n  = r_n^T rt_n
+    c64 alpha;      // alpha_n (0 when the column is done)
+    c64 alpha_prev; // alpha_{n-1}
+    c64 beta_prev;  // beta_{n-1}
+    c64 rho_next;   // rho_{n+1} (between B/C row work and finalize)
+    double rn2;     // ||rt_n||^2
+    double in_rr;   // inner CG: t^H t
+    double in_alpha, in_beta, in_tol2;
+    int32_t done, status, iters, n_active, in_done, breakdown;
+    int64_t row;    // right-hand side row j (-1: empty slot)
+    int64_t dst;    // global column index (-1: empty slot)
+};
+
+struct ShiftState {
+    c64 pi, pi_prev, pi_next; // pi_{n-1}, pi_{n-2}, pi_n at the start of A(n)
+    c64 alpha_s;
+    double resid;
+    int32_t active, conv_it;
+};
+
+struct Ctrl {
+    unsigned int arrive;  // last-CTA arrival counter (reset by the last CTA)
+    int32_t n;            // outer iteration of the panel (buffer parity)
+    int32_t k;            // inner iteration (buffer parity)
+    int32_t panel_done;
+    int32_t inner_done;
+    int32_t iter_ctr;     // outer loop executions (hard cap)
+    int32_t in_ctr;       // inner loop executions in this outer iteration (hard cap)
+    int32_t panel;        // index of the panel being solved
+    int64_t inner_total;  // inner iterations summed over the panel
+    int64_t pad[4];
+};
+
+template <typename T>
+struct Panel {
+    // matrices (values in T)
+    const int64_t *h_rp;
+    const int32_t *h_ci;
+    const T *h_val;
+    const int64_t *s_rp;
+    const int32_t *s_ci;
+    const T *s_val;
+    int64_t n_brows;
+    // panel vectors [n_rows][W] complex T
+    T *R[2], *RT, *P[2], *SP, *U, *Tv, *D[2], *Av;
+    // state
+    ColState *col;   // [W]
+    ShiftState *sh;  // [W][nz]
+    int32_t nz;
+    int32_t seed;
+    c64 zs;
+    const c64 *z;    // [nz]
+    // kept rows (projection entries) of the current panel
+    int32_t max_ent;
+    c64 *xs, *ps;    // [max_ent][nz]
+    // panel descriptors for every panel (device)
+    const int64_t *pan_row;     // [n_panels][W]  rhs row per slot (-1 empty)
+    const int64_t *pan_dst;     // [n_panels][W]  global column per slot (-1 empty)
+    const int32_t *pan_ent_ptr; // [n_panels][W+1] kept-row ranges per slot (panel-local)
+    const int64_t *pan_ent_base;// [n_panels]      offset of the panel's entries
+    const int64_t *ent_row;     // [total entries] kept row
+    const int64_t *ent_dst;     // [total entries] row index into G
+    // reductions
+    void *part;      // [W*4][ncta] partials (double or float2)
+    Ctrl *ctl;
+    cudaGraphConditionalHandle h_outer, h_inner;
+    double tol;
+    double inner_tol;
+    int32_t max_iter;
+    int32_t inner_max;
+    int32_t outer_cap;
+    int32_t in_graph; // 1: kernels run inside the solve graph and set its loop conditions
+    // outputs (device)
+    c64 *G;
+    int32_t *iters;
+    double *resid;
+    int32_t *status;
+    int64_t *stats;  // optional: [n_panels][2] = (outer iterations, inner iterations)
+};
+
+// ---------------------------------------------------------------- accumulators
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s;
+    typedef double P;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void add(const Acc &o) { s += o.s; }
+    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ P pack() const { return s; }
+    __device__ __forceinline__ static Acc unpack(P p) {
+        Acc a;
+        a.s = p;
+        return a;
+    }
+};
+// FP32 two-float (hi + lo) accumulation: TwoSum on every addition, so long
+// sums of FP32 terms keep about 48 bits without FP64 instructions.
+template <>
+struct Acc<float> {
+    float hi, lo;
+    typedef float2 P;
+    __device__ __forceinline__ void zero() { hi = lo = 0.f; }
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x;
+        const float bb = s - hi;
+        const float e = (hi - (s - bb)) + (x - bb);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ void add(const Acc &o) {
+        add(o.hi);
+        lo += o.lo;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ P pack() const { return make_float2(hi, lo); }
+    __device__ __forceinline__ static Acc unpack(P p) {
+        Acc a;
+        a.hi = p.x;
+        a.lo = p.y;
+        return a;
+    }
+};
+
+// Sums per-thread accumulators acc[CPT][K] over the CTA per column and writes
+// the CTA partials to part[(c*K + k) * gridDim.x + blockIdx.x].
+template <typename T, int W, int NT, int K>
+__device__ __forceinline__ void cta_partials(Acc<T> (&acc)[PanelVec<T>::CPT][K], void *part) {
+    using TM = Teams<T, W, NT>;
+    constexpr int CPT = TM::CPT;
+    typedef typename Acc<T>::P P;
+    __shared__ P sh[TM::PER_CTA][W * K];
+    const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[team][(lane * CPT + cc) * K + k] = acc[cc][k].pack();
+    __syncthreads();
+    for (int q = threadIdx.x; q < W * K; q += NT) {
+        Acc<T> s;
+        s.zero();
+        for (int t = 0; t < TM::PER_CTA; ++t) s.add(Acc<T>::unpack(sh[t][q]));
+        reinterpret_cast<P *>(part)[(int64_t)q * gridDim.x + blockIdx.x] = s.pack();
+    }
+    __syncthreads();
+}
+
+// Warp-wide sum of an accumulator (two-float for FP32: no FP64 instructions).
+__device__ __forceinline__ void warp_reduce(Acc<double> &s) { s.s = warp_sum(s.s); }
+__device__ __forceinline__ void warp_reduce(Acc<float> &s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Acc<float> t;
+        t.hi = __shfl_xor_sync(TB_FULL_MASK, s.hi, o);
+        t.lo = __shfl_xor_sync(TB_FULL_MASK, s.lo, o);
+        s.add(t);
+    }
+}
+
+// In the last CTA: out[q] = sum over CTAs of part[q][*] for q < W*K, one warp per q.
+template <typename T, int W, int NT, int K>
+__device__ __forceinline__ void reduce_partials(const void *part, double *out) {
+    typedef typename Acc<T>::P P;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const P *pp = reinterpret_cast<const P *>(part);
+    for (int q = warp; q < W * K; q += NT / 32) {
+        Acc<T> s;
+        s.zero();
+        for (int t = lane; t < (int)gridDim.x; t += 32) s.add(Acc<T>::unpack(__ldcg(pp + (int64_t)q * gridDim.x + t)));
+        warp_reduce(s);
+        if (lane == 0) out[q] = s.value();
+    }
+    __syncthreads();
+}
+
+// Work item index spread round-robin over the CTAs (so small per-pair loops do
+// not land on the first few SMs).
+__device__ __forceinline__ int64_t spread_index() { return (int64_t)threadIdx.x * gridDim.x + blockIdx.x; }
+
+__device__ __forceinline__ c64 cadd(c64 a, c64 b) { return a + b; }
+
+// ------------------------------------------------------------ loader functors
+// x = a(row) + s .* b(row)   (per-column complex scalars s; b may be absent)
+template <typename T, int W>
+struct LdAxpy {
+    const T *a;
+    const T *b;
+    cpx<T> s[PanelVec<T>::CPT];
+    int lane;
+    __device__ __forceinline__ void operator()(int64_t row, cpx<T> (&x)[PanelVec<T>::CPT]) const {
+        ld_row<T, W>(a, row, lane, x);
+        if (b) {
+            cpx<T> y[PanelVec<T>::CPT];
+            ld_row<T, W>(b, row, lane, y);
+#pragma unroll
+            for (int c = 0; c < PanelVec<T>::CPT; ++c) x[c] = x[c] + s[c] * y[c];
+        }
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cvt(c64 v) {
+    return mk((T)v.re, (T)v.im);
+}
+
+} // namespace tbgf

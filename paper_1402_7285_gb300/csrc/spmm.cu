@@ -1,0 +1,137 @@
+// tb_bsr_spmm: Y = A X for a real BSR matrix and a complex panel (FP64 or FP32).
+#include "spmm.cuh"
+#include "dispatch.cuh"
+
+namespace {
+
+template <typename T, int B, int W, int NT>
+__global__ void __launch_bounds__(NT) k_spmm(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                             const T *__restrict__ val, int64_t n_brows, const T *__restrict__ X,
+                                             T *__restrict__ Y) {
+    using TM = Teams<T, W, NT>;
+    constexpr int CPT = TM::CPT;
+    const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
+    int64_t r0, r1;
+    cta_rows(n_brows, blockIdx.x, gridDim.x, r0, r1);
+    auto ld = [&](int64_t row, cpx<T>(&x)[CPT]) { ld_row<T, W>(X, row, lane, x); };
+    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
+        cpx<T> acc[B][CPT];
+        bsr_row_product<T, B>(rp, ci, val, br, ld, acc);
+#pragma unroll
+        for (int i = 0; i < B; ++i) st_row<T, W>(Y, br * B + i, lane, acc[i]);
+    }
+}
+
+// dst[r][0:W] <- src[r][0:ncols] (complex), zero padded; T may be float or double.
+template <typename T>
+__global__ void k_pad_in(const double *__restrict__ src, int ncols, T *__restrict__ dst, int W, int64_t nrows) {
+    const int64_t total = nrows * W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / W;
+        const int c = (int)(t % W);
+        T re = 0, im = 0;
+        if (c < ncols) {
+            re = (T)src[(r * ncols + c) * 2];
+            im = (T)src[(r * ncols + c) * 2 + 1];
+        }
+        dst[t * 2] = re;
+        dst[t * 2 + 1] = im;
+    }
+}
+
+template <typename T>
+__global__ void k_unpad_out(const T *__restrict__ src, int W, double *__restrict__ dst, int ncols, int64_t nrows) {
+    const int64_t total = nrows * ncols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / ncols;
+        const int c = (int)(t % ncols);
+        dst[t * 2] = (double)src[(r * W + c) * 2];
+        dst[t * 2 + 1] = (double)src[(r * W + c) * 2 + 1];
+    }
+}
+
+__global__ void k_to_float(const double *__restrict__ src, float *__restrict__ dst, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = (float)src[t];
+}
+
+struct SpmmLaunch {
+    const int64_t *rp;
+    const int32_t *ci;
+    const void *val;
+    int64_t n_brows;
+    const void *X;
+    void *Y;
+    cudaStream_t s;
+    int grid;
+    template <typename T, int B, int W>
+    void run() {
+        constexpr int NT = 256;
+        using TM = Teams<T, W, NT>;
+        int64_t need = (n_brows + TM::PER_CTA - 1) / TM::PER_CTA;
+        int g = (int)(need < grid ? need : grid);
+        if (g < 1) g = 1;
+        k_spmm<T, B, W, NT><<<g, NT, 0, s>>>(rp, ci, (const T *)val, n_brows, (const T *)X, (T *)Y);
+    }
+};
+
+} // namespace
+
+namespace tbgf {
+void launch_to_float(const double *src, float *dst, int64_t n, cudaStream_t s) {
+    int g = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    if (g < 1) g = 1;
+    k_to_float<<<g, 256, 0, s>>>(src, dst, n);
+}
+} // namespace tbgf
+
+extern "C" int tb_bsr_spmm(tb_ctx *ctx, const tb_bsr *A, const double *X, int32_t ncols, double *Y,
+                           int32_t precision, void *stream) {
+    using namespace tbgf;
+    if (!ctx) return TB_ERR_ARG;
+    TB_CHECK(ctx, A && A->row_ptr && A->col_idx && A->val, TB_ERR_ARG, "tb_bsr_spmm: matrix arrays missing");
+    TB_CHECK(ctx, X && Y && ncols >= 1 && ncols <= 64, TB_ERR_ARG, "tb_bsr_spmm: ncols must be 1..64");
+    TB_CHECK(ctx, precision == TB_PREC_FP64 || precision == TB_PREC_MIXED, TB_ERR_ARG, "bad precision");
+    TB_CHECK(ctx, supported_bdim(A->bdim), TB_ERR_UNSUPPORTED, "tb_bsr_spmm: bdim %d not built", A->bdim);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = A->n_brows * A->bdim;
+    const int64_t bb = (int64_t)A->bdim * A->bdim;
+    Stager st(ctx, WS_STAGE_IN, s);
+    void *rp, *ci, *val, *x, *y;
+    st.add(A->row_ptr, sizeof(int64_t) * (A->n_brows + 1), true, false, &rp);
+    st.add(A->col_idx, sizeof(int32_t) * A->nnzb, true, false, &ci);
+    st.add(A->val, sizeof(double) * A->nnzb * bb, true, false, &val);
+    st.add(X, sizeof(double) * 2 * n * ncols, true, false, &x);
+    st.add(Y, sizeof(double) * 2 * n * ncols, false, true, &y);
+    int rc = st.commit();
+    if (rc) return rc;
+    rc = validate_bsr(ctx, (const int64_t *)rp, (const int32_t *)ci, val, A->n_brows, A->nnzb, s, "A");
+    if (rc) return rc;
+    const int W = panel_width_for(ncols);
+    const bool f32 = precision == TB_PREC_MIXED;
+    const size_t esz = f32 ? 4 : 8;
+    size_t off_val = 0, off_x = f32 ? align_up(sizeof(float) * A->nnzb * bb, 256) : 0;
+    size_t off_y = off_x + align_up(esz * 2 * n * W, 256);
+    void *wsp;
+    rc = ws_get(ctx, WS_SPMM_STAGE, off_y + esz * 2 * n * W, &wsp);
+    if (rc) return rc;
+    char *ws = (char *)wsp;
+    const void *mval = val;
+    if (f32) {
+        launch_to_float((const double *)val, (float *)(ws + off_val), A->nnzb * bb, s);
+        mval = ws + off_val;
+    }
+    int g = (int)std::min<int64_t>((n * W + 255) / 256, 152 * 16);
+    if (f32)
+        k_pad_in<float><<<g, 256, 0, s>>>((const double *)x, ncols, (float *)(ws + off_x), W, n);
+    else
+        k_pad_in<double><<<g, 256, 0, s>>>((const double *)x, ncols, (double *)(ws + off_x), W, n);
+    SpmmLaunch L{(const int64_t *)rp, (const int32_t *)ci, mval, A->n_brows, ws + off_x, ws + off_y, s, 152 * 8};
+    if (!dispatch_tbw(L, f32, A->bdim, W)) return set_error(ctx, TB_ERR_UNSUPPORTED, "no SpMM variant");
+    if (f32)
+        k_unpad_out<float><<<g, 256, 0, s>>>((const float *)(ws + off_y), W, (double *)y, ncols, n);
+    else
+        k_unpad_out<double><<<g, 256, 0, s>>>((const double *)(ws + off_y), W, (double *)y, ncols, n);
+    TB_CUDA_TRY(ctx, cudaGetLastError());
+    return st.finish();
+}

@@ -1,0 +1,123 @@
+// Block-sparse (BSR) product of a real matrix with a complex panel: the one
+// sparse product per COCG iteration that every shift shares (Sec. 3, Eq. 2).
+//
+// Panel layout: [n_rows][W] complex, row-major, (re, im) interleaved; a panel
+// row of W complex values is contiguous.  A "team" of W / CPT threads owns one
+// block row at a time: lane l holds complex columns l*CPT .. l*CPT+CPT-1, so
+// a team reads each neighbour panel row as one coalesced run of vector loads
+// (float4 = 2 complex FP32, double2 = 1 complex FP64).  The b x b block values
+// are read once per team (broadcast within the team).  Accumulation is in the
+// panel's type T.
+#pragma once
+
+#include "common.cuh"
+
+template <typename T>
+struct PanelVec;
+template <>
+struct PanelVec<float> {
+    typedef float4 V;
+    static constexpr int CPT = 2;
+};
+template <>
+struct PanelVec<double> {
+    typedef double2 V;
+    static constexpr int CPT = 1;
+};
+
+// load / store CPT complex values of one panel row for lane `lane`
+template <typename T, int W>
+__device__ __forceinline__ void ld_row(const T *__restrict__ base, int64_t row, int lane,
+                                       cpx<T> (&x)[PanelVec<T>::CPT]) {
+    typedef typename PanelVec<T>::V V;
+    const V v = *reinterpret_cast<const V *>(base + (row * W + (int64_t)lane * PanelVec<T>::CPT) * 2);
+    if constexpr (PanelVec<T>::CPT == 2) {
+        x[0] = mk(v.x, v.y);
+        x[1] = mk(v.z, v.w);
+    } else {
+        x[0] = mk(v.x, v.y);
+    }
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void st_row(T *__restrict__ base, int64_t row, int lane,
+                                       const cpx<T> (&x)[PanelVec<T>::CPT]) {
+    typedef typename PanelVec<T>::V V;
+    V v;
+    if constexpr (PanelVec<T>::CPT == 2) {
+        v.x = x[0].re, v.y = x[0].im, v.z = x[1].re, v.w = x[1].im;
+    } else {
+        v.x = x[0].re, v.y = x[0].im;
+    }
+    *reinterpret_cast<V *>(base + (row * W + (int64_t)lane * PanelVec<T>::CPT) * 2) = v;
+}
+
+// Read the B x B block at `blk` into registers (vector loads when aligned).
+template <typename T, int B>
+__device__ __forceinline__ void ld_block(const T *__restrict__ blk, T (&a)[B * B]) {
+    if constexpr ((B * B * sizeof(T)) % 16 == 0) {
+        constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+        for (int q = 0; q < B * B / PER; ++q) {
+            if constexpr (sizeof(T) == 4) {
+                float4 v = __ldg(reinterpret_cast<const float4 *>(blk) + q);
+                a[4 * q] = v.x, a[4 * q + 1] = v.y, a[4 * q + 2] = v.z, a[4 * q + 3] = v.w;
+            } else {
+                double2 v = __ldg(reinterpret_cast<const double2 *>(blk) + q);
+                a[2 * q] = v.x, a[2 * q + 1] = v.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < B * B; ++q) a[q] = __ldg(blk + q);
+    }
+}
+
+// acc[i][c] = sum over the blocks of block row br of A_blk(i, j) * v(col*B + j)[c],
+// where v(row) is produced by the loader functor `ld(row, x)`.
+template <typename T, int B, class Loader>
+__device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                const T *__restrict__ val, int64_t br, Loader &ld,
+                                                cpx<T> (&acc)[B][PanelVec<T>::CPT]) {
+    constexpr int CPT = PanelVec<T>::CPT;
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[i][c] = mk<T>(0, 0);
+    const int64_t k0 = __ldg(rp + br), k1 = __ldg(rp + br + 1);
+    for (int64_t k = k0; k < k1; ++k) {
+        const int64_t col = __ldg(ci + k);
+        cpx<T> x[B][CPT];
+#pragma unroll
+        for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
+        T a[B * B];
+        ld_block<T, B>(val + k * (int64_t)(B * B), a);
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    acc[i][c].re = fma(a[i * B + j], x[j][c].re, acc[i][c].re);
+                    acc[i][c].im = fma(a[i * B + j], x[j][c].im, acc[i][c].im);
+                }
+    }
+}
+
+// Team geometry for a CTA of NT threads and panel width W.
+template <typename T, int W, int NT>
+struct Teams {
+    static constexpr int CPT = PanelVec<T>::CPT;
+    static constexpr int TPR = W / CPT;      // threads per block row
+    static constexpr int PER_CTA = NT / TPR; // block rows in flight per CTA
+    static_assert(W % CPT == 0, "panel width must be a multiple of the vector width");
+    static_assert(NT % TPR == 0, "CTA size must be a multiple of the team size");
+};
+
+// Contiguous block-row range [r0, r1) of CTA `cta` out of `ncta`.
+__device__ __forceinline__ void cta_rows(int64_t n_brows, int cta, int ncta, int64_t &r0, int64_t &r1) {
+    const int64_t per = (n_brows + ncta - 1) / ncta;
+    r0 = (int64_t)cta * per;
+    r1 = r0 + per < n_brows ? r0 + per : n_brows;
+    if (r0 > n_brows) r0 = n_brows;
+}
