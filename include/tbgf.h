@@ -205,6 +205,68 @@ int shifted_cocg_profile(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const do
                          const int64_t *rhs_rows, int64_t n_rhs, const int64_t *out_row_ptr,
                          const int64_t *out_rows, const tb_solve_opts *opts, int32_t reps, double *ms);
 
+/* ------------------------------------------------ local subspaces (order N) */
+/* Hop-shell subspaces (Sec. 2: order-N locality): for column c the atoms
+ * within radii[c] hops of the atom owning row rhs_rows[c] in the
+ * nearest-neighbour graph of A's block pattern, ascending.  Host memory only.
+ * Two phases: with sub_atoms == NULL only sub_ptr[0..n_rhs] (CSR offsets) is
+ * written; then call again with sub_atoms sized sub_ptr[n_rhs].  radii in
+ * 0..64.  Errors: TB_ERR_ARG (ranges, or sub_ptr changed between the calls),
+ * TB_ERR_STRUCTURE (column index out of range). */
+int tb_local_subspaces(const tb_bsr *A, const int64_t *rhs_rows, const int32_t *radii, int64_t n_rhs,
+                       int64_t *sub_ptr, int32_t *sub_atoms);
+
+/* shifted_cocg_solve on truncated problems: column c solves
+ * (z_m S_OO - H_OO) x = e_j on the principal submatrices over the block rows
+ * O_c = sub_atoms[sub_ptr[c] .. sub_ptr[c+1]) (ascending, containing the atom
+ * of j = rhs_rows[c]; at most 32767 atoms) and keeps the rows out_rows (rows
+ * outside O_c give 0).  S (NULL = I) must have H's block pattern.  `order`
+ * (optional, a permutation of 0..n_rhs-1) is the order in which columns are
+ * taken from the device work queue: each CTA solves one column at a time in
+ * shared memory and takes the next as soon as it finishes.  opts->panel_w is
+ * ignored; n_z <= 1024.  Outputs and status as shifted_cocg_solve.
+ * TB_ERR_SIZE when the largest subspace does not fit one CTA's shared memory. */
+int shifted_cocg_solve_local(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, int32_t n_z,
+                             const int64_t *rhs_rows, int64_t n_rhs, const int64_t *sub_ptr,
+                             const int32_t *sub_atoms, const int64_t *out_row_ptr, const int64_t *out_rows,
+                             const int64_t *order, const tb_solve_opts *opts, double *G, int32_t *iters,
+                             double *resid, int32_t *status);
+
+/* ------------------------------------------------- learned scheduler inputs */
+/* 32 FP32 numbers per column describing its local problem (the paper has no
+ * learned component; the scheduler's predictor reads these).  Column c uses
+ * the subspace sub_atoms[sub_ptr[c]..sub_ptr[c+1]) of radius radii[c] around
+ * the atom of rhs_rows[c] (as tb_local_subspaces gives them).  Layout of
+ * out[c*32 + q]: 0 R/5; 1 log(n_atoms)/log(1000); 2..6 atoms at hop distance
+ * 1..5 / 100; 7 nearest neighbours of the atom / 12; 8 H_jj; 9..16
+ * sign(m_k)|m_k|^(1/k), m_k = e_j^T (H_OO - H_jj)^k e_j, k = 2..9; 17
+ * sum_{i!=j} S_ij^2 (0 if S = NULL); 18..21 mean, std, min, max of diag(H_OO);
+ * 22 sum_{i!=j} H_ij^2 in row j of H_OO; 23 mean Frobenius norm of the atom's
+ * in-subspace neighbour blocks; 24 rows / 1000; 25 fraction of atoms at the
+ * largest hop distance; 26..31 zero.  Moments in FP64.  S (optional) must
+ * have H's block pattern.  TB_ERR_SIZE when a subspace does not fit one CTA's
+ * shared memory. */
+int tb_descriptors(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const int64_t *rhs_rows, const int32_t *radii,
+                   int64_t n_rhs, const int64_t *sub_ptr, const int32_t *sub_atoms, float *out, void *stream);
+
+/* Iteration-count predictor: MLP 32 -> 64 -> 64 -> 1 with tanh hidden layers,
+ * FP16 weights in the forward pass, FP32 accumulation and FP32 master weights.
+ * params: mlp_param_count() floats, W1[64][32] | b1[64] | W2[64][64] | b2[64] |
+ * w3[64] | b3.  Loss: mean squared error.  Arrays: X float[n][32], y float[n]. */
+int mlp_param_count(void);
+/* Gradient of the batch loss at params (FP16-rounded forward weights), and the
+ * loss (optional). */
+int mlp_grad(tb_ctx *ctx, const float *params, const float *X, const float *y, int64_t n, float *grad,
+             double *loss, void *stream);
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on minibatches of
+ * `batch` consecutive samples, `epochs` passes in the given sample order.
+ * params: initial weights in, trained FP32 master weights out.  loss_hist
+ * (optional, double[epochs]): full-data loss after each epoch. */
+int mlp_train(tb_ctx *ctx, const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
+              float *params, double *loss_hist, void *stream);
+/* pred[i] = MLP(X[i]). */
+int mlp_predict(tb_ctx *ctx, const float *params, const float *X, int64_t n, float *pred, void *stream);
+
 /* ----------------------------------------------- Green's function -> LDOS, DM */
 /* From the output of shifted_cocg_solve (same rhs/out-row layout):
  *   ldos[c*n_z + m] = -(1/pi) Im sum_k G_{i_k j}(z_m) S_{i_k j}   (Mulliken form;

@@ -25,7 +25,8 @@ from ._lib import (TB_COL_BREAKDOWN, TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_N
                    TB_PREC_MIXED)
 
 __all__ = ["Context", "Bsr", "TbError", "build_system", "bsr_spmm", "solve", "profile", "reduce_ldos_dm",
-           "spec_to_c",
+           "spec_to_c", "local_subspaces", "solve_local", "descriptors", "mlp_grad", "mlp_train", "mlp_predict",
+           "mlp_param_count",
            "TB_PREC_FP64", "TB_PREC_MIXED", "TB_COL_CONVERGED", "TB_COL_MAX_ITER", "TB_COL_BREAKDOWN",
            "TB_COL_NONFINITE"]
 
@@ -289,6 +290,108 @@ def profile(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, ou
                                       _ptr(orows), ctypes.byref(opts), reps, ms.ctypes.data)
     ctx.check(rc, "shifted_cocg_profile")
     return {k: float(ms[i]) for i, k in enumerate(PROFILE_KERNELS)}
+
+
+def local_subspaces(H: Bsr, rhs_rows, radii):
+    """(sub_ptr int64[n+1], sub_atoms int32[...]) hop-shell subspaces (host; tb_local_subspaces)."""
+    lib = _lib.load()
+    Hn = H.numpy()
+    rhs = np.ascontiguousarray(rhs_rows, np.int64)
+    rad = np.ascontiguousarray(radii, np.int32)
+    n = int(rhs.shape[0])
+    ptr = np.zeros(n + 1, np.int64)
+    Hc = Hn.c_struct()
+    rc = lib.tb_local_subspaces(ctypes.byref(Hc), _ptr(rhs), _ptr(rad), n, _ptr(ptr), None)
+    if rc != 0:
+        raise TbError(rc, "tb_local_subspaces (sizes)")
+    atoms = np.empty(int(ptr[-1]), np.int32)
+    rc = lib.tb_local_subspaces(ctypes.byref(Hc), _ptr(rhs), _ptr(rad), n, _ptr(ptr), _ptr(atoms))
+    if rc != 0:
+        raise TbError(rc, "tb_local_subspaces")
+    return ptr, atoms
+
+
+def solve_local(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, sub_ptr, sub_atoms, out_row_ptr, out_rows,
+                *, order=None, tol=1e-10, max_iter=100000, precision=TB_PREC_FP64, seed_shift=-1, inner_tol=0.0,
+                inner_max=0) -> SolveResult:
+    """Truncated-subspace solves, one CTA per column (shifted_cocg_solve_local)."""
+    like = H.val
+    zc = _as(z, np.complex128, like=like)
+    rhs = _as(rhs_rows, np.int64, like=like)
+    sptr = _as(sub_ptr, np.int64, like=like)
+    satoms = _as(sub_atoms, np.int32, like=like)
+    optr = _as(out_row_ptr, np.int64, like=like)
+    orows = _as(out_rows, np.int64, like=like)
+    ordr = _as(order, np.int64, like=like) if order is not None else None
+    n_rhs, n_z, n_out = int(rhs.shape[0]), int(zc.shape[0]), int(optr[-1])
+    G = _empty((n_out, n_z), np.complex128, like)
+    iters = _empty((n_rhs,), np.int32, like)
+    resid = _empty((n_rhs, n_z), np.float64, like)
+    status = _empty((n_rhs,), np.int32, like)
+    stats = np.zeros(2, np.int64)
+    opts = _opts(ctx, tol, max_iter, precision, 0, seed_shift, inner_tol, inner_max, _stream_of(like), stats)
+    Hc = H.c_struct()
+    Sc = S.c_struct() if S is not None else None
+    rc = ctx.lib.shifted_cocg_solve_local(ctx.h, ctypes.byref(Hc), ctypes.byref(Sc) if Sc is not None else None,
+                                          _ptr(zc), n_z, _ptr(rhs), n_rhs, _ptr(sptr), _ptr(satoms), _ptr(optr),
+                                          _ptr(orows), _ptr(ordr), ctypes.byref(opts), _ptr(G), _ptr(iters),
+                                          _ptr(resid), _ptr(status))
+    ctx.check(rc, "shifted_cocg_solve_local")
+    return SolveResult(G, iters, resid, status, rc, int(stats[0]), int(stats[1]))
+
+
+def descriptors(ctx: Context, H: Bsr, S: Optional[Bsr], rhs_rows, radii, sub_ptr, sub_atoms):
+    """float32 [n, 32] local-environment descriptors (tb_descriptors)."""
+    like = H.val
+    rhs = _as(rhs_rows, np.int64, like=like)
+    rad = _as(radii, np.int32, like=like)
+    sptr = _as(sub_ptr, np.int64, like=like)
+    satoms = _as(sub_atoms, np.int32, like=like)
+    n = int(rhs.shape[0])
+    out = _empty((n, 32), np.float32, like)
+    Hc = H.c_struct()
+    Sc = S.c_struct() if S is not None else None
+    rc = ctx.lib.tb_descriptors(ctx.h, ctypes.byref(Hc), ctypes.byref(Sc) if Sc is not None else None, _ptr(rhs),
+                                _ptr(rad), n, _ptr(sptr), _ptr(satoms), _ptr(out), _stream_of(like))
+    ctx.check(rc, "tb_descriptors")
+    return out
+
+
+def mlp_param_count() -> int:
+    return int(_lib.load().mlp_param_count())
+
+
+def mlp_grad(ctx: Context, params, X, y):
+    """(grad float32[n_param], loss) of the mean squared error at params (host arrays)."""
+    p = np.ascontiguousarray(params, np.float32)
+    Xc = np.ascontiguousarray(X, np.float32)
+    yc = np.ascontiguousarray(y, np.float32)
+    g = np.empty_like(p)
+    loss = ctypes.c_double(0.0)
+    rc = ctx.lib.mlp_grad(ctx.h, _ptr(p), _ptr(Xc), _ptr(yc), int(Xc.shape[0]), _ptr(g), ctypes.byref(loss), None)
+    ctx.check(rc, "mlp_grad")
+    return g, float(loss.value)
+
+
+def mlp_train(ctx: Context, X, y, *, epochs, batch, lr, params):
+    """(trained float32 params, per-epoch loss) via mlp_train (host arrays)."""
+    p = np.array(params, np.float32, copy=True)
+    Xc = np.ascontiguousarray(X, np.float32)
+    yc = np.ascontiguousarray(y, np.float32)
+    hist = np.zeros(max(epochs, 1), np.float64)
+    rc = ctx.lib.mlp_train(ctx.h, _ptr(Xc), _ptr(yc), int(Xc.shape[0]), int(epochs), int(batch), float(lr), _ptr(p),
+                           _ptr(hist), None)
+    ctx.check(rc, "mlp_train")
+    return p, hist[:epochs]
+
+
+def mlp_predict(ctx: Context, params, X):
+    p = np.ascontiguousarray(params, np.float32)
+    Xc = _as(X, np.float32, like=X)
+    out = _empty((int(Xc.shape[0]),), np.float32, Xc)
+    rc = ctx.lib.mlp_predict(ctx.h, _ptr(p), _ptr(Xc), int(Xc.shape[0]), _ptr(out), _stream_of(Xc))
+    ctx.check(rc, "mlp_predict")
+    return out
 
 
 def reduce_ldos_dm(ctx: Context, G, z, w, mu: float, kT: float, rhs_rows, out_row_ptr, out_rows,

@@ -67,6 +67,15 @@ SIGNATURES = {
                                           P]),
     "shifted_cocg_profile": (ctypes.c_int, [P, PB, PB, P, ctypes.c_int32, P, ctypes.c_int64, P, P, PO,
                                             ctypes.c_int32, P]),
+    "tb_local_subspaces": (ctypes.c_int, [PB, P, P, ctypes.c_int64, P, P]),
+    "shifted_cocg_solve_local": (ctypes.c_int, [P, PB, PB, P, ctypes.c_int32, P, ctypes.c_int64, P, P, P, P, P,
+                                                PO, P, P, P, P]),
+    "tb_descriptors": (ctypes.c_int, [P, PB, PB, P, P, ctypes.c_int64, P, P, P, P]),
+    "mlp_param_count": (ctypes.c_int, []),
+    "mlp_grad": (ctypes.c_int, [P, P, P, P, ctypes.c_int64, P, P, P]),
+    "mlp_train": (ctypes.c_int, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, P, P,
+                                 P]),
+    "mlp_predict": (ctypes.c_int, [P, P, P, ctypes.c_int64, P, P]),
     "gf_reduce_ldos_dm": (ctypes.c_int, [P, P, ctypes.c_int32, P, P, ctypes.c_double, ctypes.c_double, P,
                                          ctypes.c_int64, P, P, PB, P, P, P]),
 }
