@@ -282,6 +282,32 @@ int gf_reduce_ldos_dm(tb_ctx *ctx, const double *G, int32_t n_z, const double *z
                       int64_t n_rhs, const int64_t *out_row_ptr, const int64_t *out_rows,
                       const tb_bsr *S, double *ldos, double *dm, void *stream);
 
+/* ------------------------------------------------- no-allocation variant */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot let a library allocate device memory (a pre-reserved memory arena
+ * owns every allocation, a latency-critical loop must not hit the device
+ * synchronisation of cudaFree, an embedding host forbids allocation after
+ * start-up).  Same result as gf_reduce_ldos_dm, but it calls no cudaMalloc,
+ * cudaFree or allocating routine: its scratch (one weight per kept entry and
+ * a flag) is a static device array of TB_REDUCE_STATIC_MAX_ENTRIES + 32
+ * doubles that every GPU loading the library holds until exit.
+ *  - n_out must equal out_row_ptr[n_rhs] and be <= TB_REDUCE_STATIC_MAX_ENTRIES
+ *    (else TB_ERR_SIZE, nothing queued);
+ *  - every array (G, z, w, rhs_rows, out_row_ptr, out_rows, S's arrays, ldos,
+ *    dm) must be device memory of the current device (else TB_ERR_ARG);
+ *  - the first call on a device looks up the scratch address
+ *    (cudaGetSymbolAddress) with that device current; make it before any
+ *    stream capture;
+ *  - all calls share the scratch: calls whose GPU work overlaps (other
+ *    streams or host threads) race; calls on one stream are ordered;
+ *  - with S = NULL the call synchronises the stream once to check that each
+ *    column keeps its own row. */
+#define TB_REDUCE_STATIC_MAX_ENTRIES 524288
+int gf_reduce_ldos_dm_static(tb_ctx *ctx, const double *G, int32_t n_z, const double *z, const double *w,
+                             double mu, double kT, const int64_t *rhs_rows, int64_t n_rhs,
+                             const int64_t *out_row_ptr, int64_t n_out, const int64_t *out_rows,
+                             const tb_bsr *S, double *ldos, double *dm, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

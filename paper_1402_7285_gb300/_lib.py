@@ -16,6 +16,7 @@ TB_LATTICE_SC_PERIODIC, TB_LATTICE_FCC_CLUSTER = 0, 1
 TB_ONSITE_UNIFORM, TB_ONSITE_DIAG_NORMAL = 0, 1
 TB_HOP_CONST, TB_HOP_NORMAL = 0, 1
 TB_S_IDENTITY, TB_S_NORMAL, TB_S_CONST = 0, 1, 2
+TB_REDUCE_STATIC_MAX_ENTRIES = 524288
 
 
 class TbSystemSpec(ctypes.Structure):
@@ -76,6 +77,8 @@ SIGNATURES = {
     "mlp_train": (ctypes.c_int, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, P, P,
                                  P]),
     "mlp_predict": (ctypes.c_int, [P, P, P, ctypes.c_int64, P, P]),
+    "gf_reduce_ldos_dm_static": (ctypes.c_int, [P, P, ctypes.c_int32, P, P, ctypes.c_double, ctypes.c_double,
+                                                P, ctypes.c_int64, P, ctypes.c_int64, P, PB, P, P, P]),
     "gf_reduce_ldos_dm": (ctypes.c_int, [P, P, ctypes.c_int32, P, P, ctypes.c_double, ctypes.c_double, P,
                                          ctypes.c_int64, P, P, PB, P, P, P]),
 }
