@@ -139,10 +139,14 @@ int tb_build_csr(const tb_system_spec *spec, uint64_t seed, tb_bsr *H, tb_bsr *S
 #define TB_PREC_MIXED 1 /* FP32 vectors, SpMM and updates with FP32 accumulation;
                            FP64 recurrence scalars, dot products, convergence
                            tests, projected solutions and reductions           */
+#define TB_PREC_DF64 2  /* vectors, SpMM and updates in double-float (hi + lo
+                           FP32 pairs, ~48 bits) on the FP32 pipes; FP64
+                           scalars, projections and reductions as above        */
 
 /* Y = A X for a real BSR matrix A (n = n_brows*bdim rows) and a complex panel
  * X of ncols columns: X, Y complex double [n][ncols] (row-major, interleaved).
- * precision TB_PREC_MIXED rounds A and X to FP32 and accumulates in FP32.
+ * precision TB_PREC_MIXED rounds A and X to FP32 and accumulates in FP32;
+ * TB_PREC_DF64 computes in double-float.
  * ncols in {1..64}.  The sparse product shared by every shift in each COCG
  * iteration (Sec. 3); exposed for measurement and tests. */
 int tb_bsr_spmm(tb_ctx *ctx, const tb_bsr *A, const double *X, int32_t ncols, double *Y,
@@ -153,11 +157,11 @@ typedef struct {
     double tol;          /* stop a shift when ||b - (zS-H)x|| <= tol ||b|| (recurrence
                             residual), default 1e-10                              */
     int32_t max_iter;    /* outer iterations, default 100000                        */
-    int32_t precision;   /* TB_PREC_FP64 (default) or TB_PREC_MIXED               */
+    int32_t precision;   /* TB_PREC_FP64 (default), TB_PREC_MIXED or TB_PREC_DF64 */
     int32_t panel_w;     /* columns solved together; 0 = autotuned                */
     int32_t seed_shift;  /* index of the seed shift; -1 = median Re z (default)    */
     double inner_tol;    /* S != I: relative tolerance of the inner CG on S;
-                            0 = default (1e-13 FP64, 1e-7 mixed)                  */
+                            0 = default (1e-13 FP64, 1e-12 DF64, 1e-7 mixed)      */
     int32_t inner_max;   /* S != I: inner iterations per outer iteration, 0 = 40   */
     int32_t reserved0;
     void *stream;        /* cudaStream_t to queue work on                         */

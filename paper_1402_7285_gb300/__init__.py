@@ -21,13 +21,13 @@ from typing import Any, Optional
 import numpy as np
 
 from . import _lib
-from ._lib import (TB_COL_BREAKDOWN, TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_NONFINITE, TB_PREC_FP64,
-                   TB_PREC_MIXED)
+from ._lib import (TB_COL_BREAKDOWN, TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_NONFINITE, TB_PREC_DF64,
+                   TB_PREC_FP64, TB_PREC_MIXED)
 
 __all__ = ["Context", "Bsr", "TbError", "build_system", "bsr_spmm", "solve", "profile", "reduce_ldos_dm",
            "spec_to_c", "local_subspaces", "solve_local", "descriptors", "mlp_grad", "mlp_train", "mlp_predict",
            "mlp_param_count",
-           "TB_PREC_FP64", "TB_PREC_MIXED", "TB_COL_CONVERGED", "TB_COL_MAX_ITER", "TB_COL_BREAKDOWN",
+           "TB_PREC_FP64", "TB_PREC_MIXED", "TB_PREC_DF64", "TB_COL_CONVERGED", "TB_COL_MAX_ITER", "TB_COL_BREAKDOWN",
            "TB_COL_NONFINITE"]
 
 

@@ -11,7 +11,7 @@ TB_OK = 0
 TB_ERR_ARG, TB_ERR_CUDA, TB_ERR_ALLOC, TB_ERR_UNSUPPORTED, TB_ERR_SIZE, TB_ERR_STRUCTURE = -1, -2, -3, -4, -5, -6
 TB_WARN_MAX_ITER, TB_WARN_BREAKDOWN, TB_WARN_NONFINITE = 1, 2, 4
 TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_BREAKDOWN, TB_COL_NONFINITE = 0, 1, 2, 3
-TB_PREC_FP64, TB_PREC_MIXED = 0, 1
+TB_PREC_FP64, TB_PREC_MIXED, TB_PREC_DF64 = 0, 1, 2
 TB_LATTICE_SC_PERIODIC, TB_LATTICE_FCC_CLUSTER = 0, 1
 TB_ONSITE_UNIFORM, TB_ONSITE_DIAG_NORMAL = 0, 1
 TB_HOP_CONST, TB_HOP_NORMAL = 0, 1

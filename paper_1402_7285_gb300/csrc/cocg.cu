@@ -1,823 +1,7 @@
-// shifted_cocg_solve: panel shifted COCG on the GPU (see cocg_kernels.cuh).
-#include <algorithm>
-#include <cmath>
-#include <vector>
-
-#include "cocg_kernels.cuh"
-#include "dispatch.cuh"
+// shifted_cocg_solve / shifted_cocg_profile: host driver of the panel shifted COCG.
+#include "cocg_impl.cuh"
 
 namespace tbgf {
-
-constexpr int NT = 256;
-
-// ------------------------------------------------------------------ init
-template <typename T, int W>
-__global__ void k_init_state(Panel<T> p, int has_s) {
-    const int panel = p.ctl->panel;
-    for (int c = threadIdx.x; c < W; c += blockDim.x) {
-        ColState C;
-        memset(&C, 0, sizeof(C));
-        C.row = p.pan_row[(int64_t)panel * W + c];
-        C.dst = p.pan_dst[(int64_t)panel * W + c];
-        C.alpha = mk(0.0, 0.0);
-        C.alpha_prev = mk(1.0, 0.0);
-        C.beta_prev = mk(0.0, 0.0);
-        C.rho = mk(1.0, 0.0); // S = I: rho_0 = e_j^T e_j; S != I: replaced by the init pass
-        C.rn2 = 1.0;
-        C.status = TB_COL_MAX_ITER;
-        C.n_active = p.nz;
-        if (C.row < 0) {
-            C.done = 1;
-            C.n_active = 0;
-            C.rho = mk(0.0, 0.0);
-            C.rn2 = 0.0;
-            C.status = TB_COL_CONVERGED;
-        }
-        C.in_done = 1;
-        p.col[c] = C;
-    }
-    for (int q = threadIdx.x; q < W * p.nz; q += blockDim.x) {
-        ShiftState S;
-        S.pi = S.pi_prev = S.pi_next = mk(1.0, 0.0);
-        S.alpha_s = mk(0.0, 0.0);
-        S.resid = 1.0;
-        S.active = 1;
-        S.conv_it = -1;
-        p.sh[q] = S;
-    }
-    if (threadIdx.x == 0) {
-        p.ctl->arrive = 0;
-        p.ctl->n = has_s ? 1 : 0;
-        p.ctl->k = 0;
-        p.ctl->panel_done = 0;
-        p.ctl->inner_done = 0;
-        p.ctl->iter_ctr = 0;
-        p.ctl->in_ctr = 0;
-        p.ctl->inner_total = 0;
-    }
-}
-
-template <typename T, int W>
-__global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
-    const int panel = p.ctl->panel;
-    const int64_t total = n_rows * W;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += stride) {
-        const int64_t row = t / W;
-        const int c = (int)(t % W);
-        const int64_t j = p.pan_row[(int64_t)panel * W + c];
-        const T one = (j == row) ? (T)1 : (T)0;
-        const int64_t o = t * 2;
-        p.RT[o] = one, p.RT[o + 1] = 0;
-        p.P[0][o] = p.P[0][o + 1] = 0;
-        p.P[1][o] = p.P[1][o + 1] = 0;
-        p.U[o] = p.U[o + 1] = 0;
-        if (has_s) {
-            p.R[0][o] = p.R[0][o + 1] = 0;
-            p.R[1][o] = one, p.R[1][o + 1] = 0;
-            p.SP[o] = p.SP[o + 1] = 0;
-            p.Tv[o] = p.Tv[o + 1] = 0;
-            p.D[0][o] = p.D[0][o + 1] = 0;
-            p.D[1][o] = p.D[1][o + 1] = 0;
-            p.Av[o] = p.Av[o + 1] = 0;
-        }
-    }
-    const int64_t ne = (int64_t)p.max_ent * p.nz;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ne; t += stride) {
-        p.xs[t] = mk(0.0, 0.0);
-        p.ps[t] = mk(0.0, 0.0);
-    }
-}
-
-// ------------------------------------------------------------ shifted steps
-// A(n): rotate pi, test ||rt_n|| / |pi_n| <= tol, then p^m_n on the kept rows.
-template <typename T, int W>
-__device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) {
-    const int panel = p.ctl->panel;
-    const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
-    const int64_t ebase = p.pan_ent_base[panel];
-    const int pairs = W * p.nz;
-    for (int q = (int)spread_index(); q < pairs; q += gridDim.x * blockDim.x) {
-        const int c = q / p.nz, m = q % p.nz;
-        ColState &C = p.col[c];
-        if (C.done) continue;
-        ShiftState &S = p.sh[q];
-        if (!S.active) continue;
-        S.pi_prev = S.pi;
-        S.pi = S.pi_next;
-        const double res = sqrt(C.rn2) / sqrt(cabs2(S.pi));
-        S.resid = res;
-        if (res <= p.tol) {
-            S.active = 0;
-            S.conv_it = n;
-            atomicSub(&C.n_active, 1);
-            continue;
-        }
-        const c64 ratio = cdiv(S.pi_prev, S.pi);
-        const c64 bs = (ratio * ratio) * C.beta_prev;
-        const c64 ipi = cdiv(mk(1.0, 0.0), S.pi);
-        for (int e = eptr[c]; e < eptr[c + 1]; ++e) {
-            const int64_t row = p.ent_row[ebase + e];
-            const T *rp = Rc + (row * W + c) * 2;
-            const c64 rv = mk((double)rp[0], (double)rp[1]);
-            c64 *ps = p.ps + (int64_t)e * p.nz + m;
-            *ps = ipi * rv + bs * (*ps);
-        }
-    }
-}
-
-// B(n) / B'(n): pi_{n+1}, alpha^m_n and x^m += alpha^m_n p^m_n on the kept rows.
-template <typename T, int W>
-__device__ void pair_step_B(const Panel<T> &p) {
-    const int panel = p.ctl->panel;
-    const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
-    const int pairs = W * p.nz;
-    for (int q = (int)spread_index(); q < pairs; q += gridDim.x * blockDim.x) {
-        const int c = q / p.nz, m = q % p.nz;
-        ColState &C = p.col[c];
-        if (C.done) continue;
-        ShiftState &S = p.sh[q];
-        if (!S.active) continue;
-        const c64 sig = p.z[m] - p.zs;
-        const c64 coef = cdiv(C.alpha * C.beta_prev, C.alpha_prev);
-        const c64 one = mk(1.0, 0.0);
-        const c64 pn = (one + C.alpha * sig) * S.pi + coef * (S.pi - S.pi_prev);
-        const c64 as = cdiv(S.pi, pn) * C.alpha;
-        if (!cfinite(pn) || (pn.re == 0.0 && pn.im == 0.0) || !cfinite(as)) {
-            S.active = 0;
-            S.resid = nan("");
-            C.breakdown = 1;
-            atomicSub(&C.n_active, 1);
-            continue;
-        }
-        S.pi_next = pn;
-        S.alpha_s = as;
-        for (int e = eptr[c]; e < eptr[c + 1]; ++e) {
-            c64 *xs = p.xs + (int64_t)e * p.nz + m;
-            *xs = *xs + as * p.ps[(int64_t)e * p.nz + m];
-        }
-    }
-}
-
-// -------------------------------------------------------------- kernel A
-template <typename T, int B, int W, bool HAS_S>
-__global__ void __launch_bounds__(NT) k_outer(Panel<T> p) {
-    using TM = Teams<T, W, NT>;
-    constexpr int CPT = TM::CPT;
-    const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
-    const int n = p.ctl->n;
-    const T *Rc = HAS_S ? p.R[n & 1] : p.RT;
-    T *Pnew = p.P[n & 1];
-    LdAxpy<T, W> ld;
-    ld.a = Rc;
-    ld.b = p.P[(n + 1) & 1];
-    ld.lane = lane;
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) {
-        const ColState &C = p.col[lane * CPT + cc];
-        ld.s[cc] = C.done ? mk<T>(0, 0) : cvt<T>(C.beta_prev);
-    }
-    const cpx<T> zs = cvt<T>(p.zs);
-    Acc<T> acc[CPT][2];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
-        cpx<T> y[B][CPT];
-        bsr_row_product<T, B>(p.h_rp, p.h_ci, p.h_val, br, ld, y);
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const int64_t row = br * B + i;
-            cpx<T> pv[CPT], u[CPT];
-            ld(row, pv);
-            st_row<T, W>(Pnew, row, lane, pv);
-            if constexpr (HAS_S) {
-                cpx<T> rt[CPT], sp[CPT];
-                ld_row<T, W>(p.RT, row, lane, rt);
-                ld_row<T, W>(p.SP, row, lane, sp);
-#pragma unroll
-                for (int cc = 0; cc < CPT; ++cc) {
-                    sp[cc] = rt[cc] + ld.s[cc] * sp[cc];
-                    u[cc] = zs * sp[cc] - y[i][cc];
-                }
-                st_row<T, W>(p.SP, row, lane, sp);
-            } else {
-#pragma unroll
-                for (int cc = 0; cc < CPT; ++cc) u[cc] = zs * pv[cc] - y[i][cc];
-            }
-            st_row<T, W>(p.U, row, lane, u);
-#pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                acc[cc][0].add(pv[cc].re * u[cc].re);
-                acc[cc][0].add(-(pv[cc].im * u[cc].im));
-                acc[cc][1].add(pv[cc].re * u[cc].im);
-                acc[cc][1].add(pv[cc].im * u[cc].re);
-            }
-        }
-    }
-    cta_partials<T, W, NT, 2>(acc, p.part);
-    pair_step_A<T, W>(p, Rc, n);
-    if (!last_cta_arrival(&p.ctl->arrive)) return;
-    // ---- last CTA: alpha_n = rho_n / mu_n; column and panel completion
-    __shared__ double red[W * 2];
-    reduce_partials<T, W, NT, 2>(p.part, red);
-    for (int c = threadIdx.x; c < W; c += NT) {
-        ColState &C = p.col[c];
-        if (C.done) continue;
-        const c64 mu = mk(red[2 * c], red[2 * c + 1]);
-        const int n_active = atomicAdd(&C.n_active, 0);
-        int st = -1;
-        if (n_active <= 0)
-            st = C.breakdown ? TB_COL_BREAKDOWN : TB_COL_CONVERGED;
-        else if (!cfinite(mu) || !cfinite(C.rho))
-            st = TB_COL_NONFINITE;
-        else if ((mu.re == 0.0 && mu.im == 0.0) || (C.rho.re == 0.0 && C.rho.im == 0.0))
-            st = TB_COL_BREAKDOWN;
-        else if (C.iters >= p.max_iter)
-            st = TB_COL_MAX_ITER;
-        c64 a = mk(0.0, 0.0);
-        if (st < 0) {
-            a = cdiv(C.rho, mu);
-            if (!cfinite(a)) st = TB_COL_NONFINITE;
-        }
-        if (st >= 0) {
-            C.done = 1;
-            C.status = st;
-            C.alpha = mk(0.0, 0.0);
-        } else {
-            C.alpha = a;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int all = 1;
-        for (int c = 0; c < W; ++c) all &= (p.col[c].done != 0);
-        p.ctl->panel_done = all;
-    }
-}
-
-// Common end of an outer iteration (last CTA): beta_n, rotation, loop condition.
-template <typename T, int W>
-__device__ void finish_outer(const Panel<T> &p, const double *rho_next, int init) {
-    for (int c = threadIdx.x; c < W; c += NT) {
-        ColState &C = p.col[c];
-        if (C.done) continue;
-        const c64 rn = mk(rho_next[2 * c], rho_next[2 * c + 1]);
-        if (init) {
-            C.rho = rn;
-            continue;
-        }
-        C.beta_prev = cdiv(rn, C.rho);
-        C.alpha_prev = C.alpha;
-        C.rho = rn;
-        C.iters += 1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (init) {
-            p.ctl->n = 0;
-        } else {
-            p.ctl->n += 1;
-            p.ctl->iter_ctr += 1;
-            const int cont = (!p.ctl->panel_done) && (p.ctl->iter_ctr < p.outer_cap);
-            if (p.in_graph) cudaGraphSetConditional(p.h_outer, cont ? 1u : 0u);
-        }
-    }
-}
-
-// -------------------------------------------------------------- kernel B (S = I)
-template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT) k_update_sI(Panel<T> p) {
-    using TM = Teams<T, W, NT>;
-    constexpr int CPT = TM::CPT;
-    const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
-    cpx<T> a[CPT];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) a[cc] = cvt<T>(p.col[lane * CPT + cc].alpha);
-    Acc<T> acc[CPT][3];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero(), acc[cc][2].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const int64_t row = br * B + i;
-            cpx<T> rt[CPT], u[CPT];
-            ld_row<T, W>(p.RT, row, lane, rt);
-            ld_row<T, W>(p.U, row, lane, u);
-#pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                rt[cc] = rt[cc] - a[cc] * u[cc];
-                const T rr = rt[cc].re * rt[cc].re, ii = rt[cc].im * rt[cc].im;
-                acc[cc][0].add(rr);
-                acc[cc][0].add(-ii);
-                acc[cc][1].add((T)2 * rt[cc].re * rt[cc].im);
-                acc[cc][2].add(rr);
-                acc[cc][2].add(ii);
-            }
-            st_row<T, W>(p.RT, row, lane, rt);
-        }
-    }
-    cta_partials<T, W, NT, 3>(acc, p.part);
-    pair_step_B<T, W>(p);
-    if (!last_cta_arrival(&p.ctl->arrive)) return;
-    __shared__ double red[W * 3];
-    reduce_partials<T, W, NT, 3>(p.part, red);
-    __shared__ double rho_next[W * 2];
-    for (int c = threadIdx.x; c < W; c += NT) {
-        rho_next[2 * c] = red[3 * c];
-        rho_next[2 * c + 1] = red[3 * c + 1];
-        if (!p.col[c].done) p.col[c].rn2 = red[3 * c + 2];
-    }
-    __syncthreads();
-    finish_outer<T, W>(p, rho_next, 0);
-}
-
-// -------------------------------------------------------------- kernel B' (S != I)
-template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT) k_update_S(Panel<T> p) {
-    using TM = Teams<T, W, NT>;
-    constexpr int CPT = TM::CPT;
-    const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
-    const int n = p.ctl->n;
-    const T *Rc = p.R[n & 1];
-    T *Rn = p.R[(n + 1) & 1];
-    LdAxpy<T, W> ld; // y_0 = r_n - alpha_n u
-    ld.a = Rc;
-    ld.b = p.U;
-    ld.lane = lane;
-    cpx<T> a[CPT];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) {
-        a[cc] = cvt<T>(p.col[lane * CPT + cc].alpha);
-        ld.s[cc] = mk<T>(-a[cc].re, -a[cc].im);
-    }
-    Acc<T> acc[CPT][2];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
-        cpx<T> sy[B][CPT];
-        bsr_row_product<T, B>(p.s_rp, p.s_ci, p.s_val, br, ld, sy);
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const int64_t row = br * B + i;
-            cpx<T> rt[CPT], u[CPT], y0[CPT], t[CPT];
-            ld_row<T, W>(p.RT, row, lane, rt);
-            ld_row<T, W>(p.U, row, lane, u);
-            ld(row, y0);
-#pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                rt[cc] = rt[cc] - a[cc] * u[cc];
-                t[cc] = rt[cc] - sy[i][cc];
-                acc[cc][0].add(rt[cc].re * rt[cc].re);
-                acc[cc][0].add(rt[cc].im * rt[cc].im);
-                acc[cc][1].add(t[cc].re * t[cc].re);
-                acc[cc][1].add(t[cc].im * t[cc].im);
-            }
-            st_row<T, W>(p.RT, row, lane, rt);
-            st_row<T, W>(Rn, row, lane, y0);
-            st_row<T, W>(p.Tv, row, lane, t);
-        }
-    }
-    cta_partials<T, W, NT, 2>(acc, p.part);
-    pair_step_B<T, W>(p);
-    if (!last_cta_arrival(&p.ctl->arrive)) return;
-    __shared__ double red[W * 2];
-    reduce_partials<T, W, NT, 2>(p.part, red);
-    __shared__ int all_done;
-    if (threadIdx.x == 0) all_done = 1;
-    __syncthreads();
-    for (int c = threadIdx.x; c < W; c += NT) {
-        ColState &C = p.col[c];
-        C.in_alpha = 0.0;
-        C.in_beta = 0.0;
-        if (C.done) {
-            C.in_done = 1;
-            continue;
-        }
-        C.rn2 = red[2 * c];
-        C.in_rr = red[2 * c + 1];
-        C.in_tol2 = p.inner_tol * p.inner_tol * C.rn2;
-        C.in_done = (C.in_rr <= C.in_tol2) ? 1 : 0;
-        if (!C.in_done) atomicAnd(&all_done, 0);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        p.ctl->k = 0;
-        p.ctl->in_ctr = 0;
-        p.ctl->inner_done = all_done;
-        if (p.in_graph) cudaGraphSetConditional(p.h_inner, (!all_done && p.inner_max > 0) ? 1u : 0u);
-    }
-}
-
-// ------------------------------------------------------- inner CG on S: IC_A
-template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT) k_inner_a(Panel<T> p) {
-    using TM = Teams<T, W, NT>;
-    constexpr int CPT = TM::CPT;
-    const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
-    const int k = p.ctl->k;
-    T *Dn = p.D[k & 1];
-    LdAxpy<T, W> ld; // d_k = t_k + beta d_{k-1}
-    ld.a = p.Tv;
-    ld.b = (k == 0) ? nullptr : p.D[(k + 1) & 1];
-    ld.lane = lane;
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) ld.s[cc] = mk<T>((T)p.col[lane * CPT + cc].in_beta, 0);
-    Acc<T> acc[CPT][1];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
-        cpx<T> sd[B][CPT];
-        bsr_row_product<T, B>(p.s_rp, p.s_ci, p.s_val, br, ld, sd);
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const int64_t row = br * B + i;
-            cpx<T> d[CPT];
-            ld(row, d);
-            st_row<T, W>(Dn, row, lane, d);
-            st_row<T, W>(p.Av, row, lane, sd[i]);
-#pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                acc[cc][0].add(d[cc].re * sd[i][cc].re);
-                acc[cc][0].add(d[cc].im * sd[i][cc].im);
-            }
-        }
-    }
-    cta_partials<T, W, NT, 1>(acc, p.part);
-    if (!last_cta_arrival(&p.ctl->arrive)) return;
-    __shared__ double red[W];
-    reduce_partials<T, W, NT, 1>(p.part, red);
-    for (int c = threadIdx.x; c < W; c += NT) {
-        ColState &C = p.col[c];
-        if (C.in_done) {
-            C.in_alpha = 0.0;
-            continue;
-        }
-        const double dad = red[c];
-        if (!(dad > 0.0) || !isfinite(dad)) { // S not positive definite on this direction
-            C.in_done = 1;
-            C.in_alpha = 0.0;
-            continue;
-        }
-        C.in_alpha = C.in_rr / dad;
-    }
-}
-
-// ------------------------------------------------------- inner CG on S: IC_B
-template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT) k_inner_b(Panel<T> p) {
-    using TM = Teams<T, W, NT>;
-    constexpr int CPT = TM::CPT;
-    const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
-    const int k = p.ctl->k;
-    const int n = p.ctl->n;
-    const T *D = p.D[k & 1];
-    T *Y = p.R[(n + 1) & 1];
-    cpx<T> a[CPT];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) a[cc] = mk<T>((T)p.col[lane * CPT + cc].in_alpha, 0);
-    Acc<T> acc[CPT][1];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const int64_t row = br * B + i;
-            cpx<T> y[CPT], d[CPT], t[CPT], av[CPT];
-            ld_row<T, W>(Y, row, lane, y);
-            ld_row<T, W>(D, row, lane, d);
-            ld_row<T, W>(p.Tv, row, lane, t);
-            ld_row<T, W>(p.Av, row, lane, av);
-#pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                y[cc] = y[cc] + a[cc] * d[cc];
-                t[cc] = t[cc] - a[cc] * av[cc];
-                acc[cc][0].add(t[cc].re * t[cc].re);
-                acc[cc][0].add(t[cc].im * t[cc].im);
-            }
-            st_row<T, W>(Y, row, lane, y);
-            st_row<T, W>(p.Tv, row, lane, t);
-        }
-    }
-    cta_partials<T, W, NT, 1>(acc, p.part);
-    if (!last_cta_arrival(&p.ctl->arrive)) return;
-    __shared__ double red[W];
-    reduce_partials<T, W, NT, 1>(p.part, red);
-    __shared__ int all_done;
-    if (threadIdx.x == 0) all_done = 1;
-    __syncthreads();
-    for (int c = threadIdx.x; c < W; c += NT) {
-        ColState &C = p.col[c];
-        if (!C.in_done) {
-            const double tt = red[c];
-            C.in_beta = tt / C.in_rr;
-            C.in_rr = tt;
-            if (tt <= C.in_tol2 || !isfinite(tt)) C.in_done = 1;
-        }
-        if (!C.in_done) atomicAnd(&all_done, 0);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        p.ctl->k += 1;
-        p.ctl->in_ctr += 1;
-        p.ctl->inner_total += 1;
-        p.ctl->inner_done = all_done;
-        const int cont = (!all_done) && (p.ctl->in_ctr < p.inner_max);
-        if (p.in_graph) cudaGraphSetConditional(p.h_inner, cont ? 1u : 0u);
-    }
-}
-
-// -------------------------------------------------------------- kernel C (S != I)
-template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT) k_rho(Panel<T> p, int init) {
-    using TM = Teams<T, W, NT>;
-    constexpr int CPT = TM::CPT;
-    const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
-    const int n = p.ctl->n;
-    const T *Rn = p.R[(n + 1) & 1];
-    Acc<T> acc[CPT][2];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const int64_t row = br * B + i;
-            cpx<T> r[CPT], rt[CPT];
-            ld_row<T, W>(Rn, row, lane, r);
-            ld_row<T, W>(p.RT, row, lane, rt);
-#pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                acc[cc][0].add(r[cc].re * rt[cc].re);
-                acc[cc][0].add(-(r[cc].im * rt[cc].im));
-                acc[cc][1].add(r[cc].re * rt[cc].im);
-                acc[cc][1].add(r[cc].im * rt[cc].re);
-            }
-        }
-    }
-    cta_partials<T, W, NT, 2>(acc, p.part);
-    if (!last_cta_arrival(&p.ctl->arrive)) return;
-    __shared__ double red[W * 2];
-    reduce_partials<T, W, NT, 2>(p.part, red);
-    finish_outer<T, W>(p, red, init);
-}
-
-// -------------------------------------------------------------- write-out
-template <typename T, int W>
-__global__ void k_writeout(Panel<T> p) {
-    const int panel = p.ctl->panel;
-    const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
-    const int64_t ebase = p.pan_ent_base[panel];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t ne = (int64_t)eptr[W] * p.nz;
-    for (int64_t t = tid; t < ne; t += stride) {
-        const int64_t e = t / p.nz;
-        const int m = (int)(t % p.nz);
-        p.G[p.ent_dst[ebase + e] * p.nz + m] = p.xs[t];
-    }
-    for (int64_t q = tid; q < (int64_t)W * p.nz; q += stride) {
-        const int c = (int)(q / p.nz), m = (int)(q % p.nz);
-        const int64_t dst = p.col[c].dst;
-        if (dst >= 0) p.resid[dst * p.nz + m] = p.sh[q].resid;
-    }
-    if (tid < W) {
-        const ColState &C = p.col[tid];
-        if (C.dst >= 0) {
-            p.iters[C.dst] = C.iters;
-            p.status[C.dst] = C.done ? C.status : TB_COL_MAX_ITER;
-        }
-    }
-    if (last_cta_arrival(&p.ctl->arrive) && threadIdx.x == 0) {
-        if (p.stats) {
-            p.stats[2 * panel] = p.ctl->iter_ctr;
-            p.stats[2 * panel + 1] = p.ctl->inner_total;
-        }
-        p.ctl->panel = panel + 1;
-    }
-}
-
-// ================================================================== host side
-struct GraphBuilder {
-    tb_ctx *ctx;
-    int rc = TB_OK;
-    cudaGraphNode_t add_kernel(cudaGraph_t g, const void *fn, dim3 grid, dim3 block, void **args,
-                               const cudaGraphNode_t *deps, int ndeps) {
-        if (rc) return nullptr;
-        cudaKernelNodeParams kp;
-        std::memset(&kp, 0, sizeof(kp));
-        kp.func = const_cast<void *>(fn);
-        kp.gridDim = grid;
-        kp.blockDim = block;
-        kp.sharedMemBytes = 0;
-        kp.kernelParams = args;
-        cudaGraphNode_t node = nullptr;
-        cudaError_t e = cudaGraphAddKernelNode(&node, g, deps, ndeps, &kp);
-        if (e != cudaSuccess) rc = set_error(ctx, TB_ERR_CUDA, "cudaGraphAddKernelNode: %s", cudaGetErrorString(e));
-        return node;
-    }
-    cudaGraphNode_t add_while(cudaGraph_t g, cudaGraphConditionalHandle h, const cudaGraphNode_t *deps, int ndeps,
-                              cudaGraph_t *body) {
-        if (rc) return nullptr;
-        // the parameter union has no default constructor: use zeroed raw storage
-        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
-        std::memset(raw, 0, sizeof(raw));
-        cudaGraphNodeParams *np = reinterpret_cast<cudaGraphNodeParams *>(raw);
-        np->type = cudaGraphNodeTypeConditional;
-        np->conditional.handle = h;
-        np->conditional.type = cudaGraphCondTypeWhile;
-        np->conditional.size = 1;
-        cudaGraphNode_t node = nullptr;
-        cudaError_t e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, np);
-        if (e != cudaSuccess) {
-            rc = set_error(ctx, TB_ERR_CUDA, "conditional node: %s", cudaGetErrorString(e));
-            return nullptr;
-        }
-        *body = np->conditional.phGraph_out[0];
-        return node;
-    }
-    cudaGraphConditionalHandle handle(cudaGraph_t g, unsigned def, unsigned flags) {
-        cudaGraphConditionalHandle h = 0;
-        if (rc) return h;
-        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, def, flags);
-        if (e != cudaSuccess) rc = set_error(ctx, TB_ERR_CUDA, "conditional handle: %s", cudaGetErrorString(e));
-        return h;
-    }
-};
-
-struct SolveLaunch {
-    tb_ctx *ctx;
-    bool has_s;
-    int ncta;
-    int64_t n_rows;
-    int n_panels;
-    cudaStream_t stream;
-    int profile_reps; // > 0: time the kernels of the first panel instead of solving
-    double *ms_out;   // [8] average ms per launch (profile)
-    Panel<double> pd; // type-erased panel (all T-dependent members are pointers)
-    int rc = TB_OK;
-
-    int vec_grid(int W) const {
-        return (int)std::min<int64_t>(std::max<int64_t>((n_rows * W + NT - 1) / NT, 1), 152 * 8);
-    }
-
-    template <typename T, int B, int W>
-    void run() {
-        Panel<T> p;
-        static_assert(sizeof(Panel<T>) == sizeof(Panel<double>), "panel layout");
-        std::memcpy(&p, &pd, sizeof(p));
-        if (profile_reps > 0)
-            profile<T, B, W>(p);
-        else
-            solve_graph<T, B, W>(p);
-    }
-
-    template <typename T, int B, int W>
-    void profile(Panel<T> p) {
-        p.in_graph = 0;
-        const dim3 grid(ncta), block(NT);
-        const int has_s_i = has_s ? 1 : 0;
-        k_init_state<T, W><<<1, NT, 0, stream>>>(p, has_s_i);
-        k_init_vec<T, W><<<vec_grid(W), NT, 0, stream>>>(p, n_rows, has_s_i);
-        if (has_s) {
-            k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
-            k_inner_a<T, B, W><<<grid, block, 0, stream>>>(p);
-            k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
-            k_rho<T, B, W><<<grid, block, 0, stream>>>(p, 1);
-        }
-        cudaEvent_t ev[6];
-        for (auto &e : ev) cudaEventCreate(&e);
-        double acc[5] = {0, 0, 0, 0, 0};
-        for (int r = 0; r < profile_reps && !rc; ++r) {
-            cudaEventRecord(ev[0], stream);
-            if (has_s)
-                k_outer<T, B, W, true><<<grid, block, 0, stream>>>(p);
-            else
-                k_outer<T, B, W, false><<<grid, block, 0, stream>>>(p);
-            cudaEventRecord(ev[1], stream);
-            if (has_s)
-                k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
-            else
-                k_update_sI<T, B, W><<<grid, block, 0, stream>>>(p);
-            cudaEventRecord(ev[2], stream);
-            int nev = 3;
-            if (has_s) {
-                k_inner_a<T, B, W><<<grid, block, 0, stream>>>(p);
-                cudaEventRecord(ev[3], stream);
-                k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
-                cudaEventRecord(ev[4], stream);
-                k_rho<T, B, W><<<grid, block, 0, stream>>>(p, 0);
-                cudaEventRecord(ev[5], stream);
-                nev = 6;
-            }
-            cudaError_t e = cudaEventSynchronize(ev[nev - 1]);
-            if (e != cudaSuccess) {
-                rc = set_error(ctx, TB_ERR_CUDA, "profile: %s", cudaGetErrorString(e));
-                break;
-            }
-            const int map[5] = {0, 1, 2, 3, 4};
-            for (int k = 0; k + 1 < nev; ++k) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-                acc[map[k]] += ms;
-            }
-        }
-        for (auto &e : ev) cudaEventDestroy(e);
-        for (int k = 0; k < 8; ++k) ms_out[k] = 0.0;
-        for (int k = 0; k < 5; ++k) ms_out[k] = acc[k] / profile_reps;
-        if (!has_s) ms_out[2] = ms_out[3] = ms_out[4] = 0.0;
-    }
-
-    template <typename T, int B, int W>
-    void solve_graph(Panel<T> p) {
-        p.in_graph = 1;
-        GraphBuilder gb{ctx};
-        cudaGraph_t g = nullptr;
-        if (cudaGraphCreate(&g, 0) != cudaSuccess) {
-            rc = set_error(ctx, TB_ERR_CUDA, "cudaGraphCreate");
-            return;
-        }
-        p.h_outer = gb.handle(g, 1u, cudaGraphCondAssignDefault);
-        cudaGraphConditionalHandle h_inner_init = has_s ? gb.handle(g, 0u, 0u) : 0;
-        const dim3 grid(ncta), block(NT);
-        int has_s_i = has_s ? 1 : 0;
-        int init1 = 1, init0 = 0;
-        int64_t nr = n_rows;
-        // kernel arguments are copied when each node is added
-        Panel<T> p_init = p;
-        p_init.h_inner = h_inner_init;
-        void *a_state[] = {&p, &has_s_i};
-        void *a_vec[] = {&p, &nr, &has_s_i};
-        cudaGraphNode_t n_state = gb.add_kernel(g, (const void *)k_init_state<T, W>, dim3(1), block, a_state, nullptr, 0);
-        cudaGraphNode_t last = gb.add_kernel(g, (const void *)k_init_vec<T, W>, dim3(vec_grid(W)), block, a_vec, &n_state, 1);
-        void *a_pinit[] = {&p_init};
-        void *a_pinit_rho[] = {&p_init, &init1};
-        if (has_s) {
-            last = gb.add_kernel(g, (const void *)k_update_S<T, B, W>, grid, block, a_pinit, &last, 1);
-            cudaGraph_t ib = nullptr;
-            last = gb.add_while(g, h_inner_init, &last, 1, &ib);
-            if (!gb.rc) {
-                cudaGraphNode_t x = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid, block, a_pinit, nullptr, 0);
-                gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_pinit, &x, 1);
-            }
-            last = gb.add_kernel(g, (const void *)k_rho<T, B, W>, grid, block, a_pinit_rho, &last, 1);
-        }
-        cudaGraph_t ob = nullptr;
-        cudaGraphNode_t outer = gb.add_while(g, p.h_outer, &last, 1, &ob);
-        Panel<T> p_body = p;
-        void *a_body[] = {&p_body};
-        void *a_body_rho[] = {&p_body, &init0};
-        if (!gb.rc) {
-            if (has_s) {
-                p_body.h_inner = gb.handle(ob, 0u, 0u);
-                cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, true>, grid, block, a_body, nullptr, 0);
-                x = gb.add_kernel(ob, (const void *)k_update_S<T, B, W>, grid, block, a_body, &x, 1);
-                cudaGraph_t ib = nullptr;
-                x = gb.add_while(ob, p_body.h_inner, &x, 1, &ib);
-                if (!gb.rc) {
-                    cudaGraphNode_t y = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid, block, a_body, nullptr, 0);
-                    gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_body, &y, 1);
-                }
-                gb.add_kernel(ob, (const void *)k_rho<T, B, W>, grid, block, a_body_rho, &x, 1);
-            } else {
-                cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, false>, grid, block, a_body, nullptr, 0);
-                gb.add_kernel(ob, (const void *)k_update_sI<T, B, W>, grid, block, a_body, &x, 1);
-            }
-        }
-        void *a_out[] = {&p};
-        gb.add_kernel(g, (const void *)k_writeout<T, W>, dim3(152 * 2), block, a_out, &outer, 1);
-        if (gb.rc) {
-            rc = gb.rc;
-            cudaGraphDestroy(g);
-            return;
-        }
-        cudaGraphExec_t exec = nullptr;
-        cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
-        if (e != cudaSuccess) {
-            rc = set_error(ctx, TB_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
-            cudaGraphDestroy(g);
-            return;
-        }
-        for (int i = 0; i < n_panels && !rc; ++i) {
-            e = cudaGraphLaunch(exec, stream);
-            if (e != cudaSuccess) rc = set_error(ctx, TB_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
-        }
-        e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess && !rc) rc = set_error(ctx, TB_ERR_CUDA, "solve: %s", cudaGetErrorString(e));
-        cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(g);
-    }
-};
 
 __global__ void k_copy_z(const double *z, c64 *zc, int nz) {
     for (int i = threadIdx.x; i < nz; i += blockDim.x) zc[i] = mk(z[2 * i], z[2 * i + 1]);
@@ -878,7 +62,8 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
              TB_ERR_ARG, "S does not match H");
     TB_CHECK(ctx, z && n_z >= 1 && n_z <= 4096, TB_ERR_ARG, "n_z must be 1..4096");
     TB_CHECK(ctx, n_rhs >= 0 && (n_rhs == 0 || (rhs_rows && out_row_ptr)), TB_ERR_ARG, "rhs arrays missing");
-    TB_CHECK(ctx, opts.precision == TB_PREC_FP64 || opts.precision == TB_PREC_MIXED, TB_ERR_ARG, "bad precision");
+    TB_CHECK(ctx, opts.precision == TB_PREC_FP64 || opts.precision == TB_PREC_MIXED || opts.precision == TB_PREC_DF64,
+             TB_ERR_ARG, "bad precision");
     TB_CHECK(ctx, opts.tol > 0.0 && opts.max_iter >= 0, TB_ERR_ARG, "tol must be > 0 and max_iter >= 0");
     TB_CHECK(ctx, opts.panel_w == 0 || opts.panel_w == 8 || opts.panel_w == 16 || opts.panel_w == 32 ||
                       opts.panel_w == 64,
@@ -889,6 +74,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     if (n_rhs == 0) return TB_OK;
     cudaStream_t stream = (cudaStream_t)opts.stream;
     const bool mixed = opts.precision == TB_PREC_MIXED;
+    const bool lowp = opts.precision != TB_PREC_FP64; // matrix values converted to FP32 or df
     const bool has_s = S != nullptr;
     const int b = H->bdim;
     const int64_t n_rows = H->n_brows * b;
@@ -996,8 +182,9 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const size_t o_erow = take(sizeof(int64_t) * std::max<int64_t>(n_out, 1));
     const size_t o_edst = take(sizeof(int64_t) * ent_dst.size());
     const size_t o_stats = take(sizeof(int64_t) * 2 * n_panels);
-    const size_t o_h32 = mixed ? take(sizeof(float) * H->nnzb * bb) : 0;
-    const size_t o_s32 = (mixed && has_s) ? take(sizeof(float) * S->nnzb * bb) : 0;
+    const size_t vsz = mixed ? sizeof(float) : sizeof(double);
+    const size_t o_h32 = lowp ? take(vsz * H->nnzb * bb) : 0;
+    const size_t o_s32 = (lowp && has_s) ? take(vsz * S->nnzb * bb) : 0;
     void *small_base = nullptr;
     rc = ws_get(ctx, WS_SOLVE_SMALL, off, &small_base);
     if (rc) return rc;
@@ -1017,11 +204,11 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_edst, ent_dst.data(), sizeof(int64_t) * ent_dst.size(), cudaMemcpyHostToDevice, stream));
     k_copy_z<<<1, 256, 0, stream>>>((const double *)d_z, (c64 *)(sb + o_zc), n_z);
     const void *hval = d_hval, *sval = d_sval;
-    if (mixed) {
-        launch_to_float((const double *)d_hval, (float *)(sb + o_h32), H->nnzb * bb, stream);
+    if (lowp) {
+        convert_values(opts.precision, (const double *)d_hval, sb + o_h32, H->nnzb * bb, stream);
         hval = sb + o_h32;
         if (has_s) {
-            launch_to_float((const double *)d_sval, (float *)(sb + o_s32), S->nnzb * bb, stream);
+            convert_values(opts.precision, (const double *)d_sval, sb + o_s32, S->nnzb * bb, stream);
             sval = sb + o_s32;
         }
     }
@@ -1072,7 +259,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.part = sb + o_part;
     p.ctl = (Ctrl *)(sb + o_ctl);
     p.tol = opts.tol;
-    p.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : (mixed ? 1e-7 : 1e-13);
+    p.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : (mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13));
     p.max_iter = opts.max_iter;
     p.inner_max = opts.inner_max > 0 ? opts.inner_max : 40;
     p.outer_cap = opts.max_iter + 2;
@@ -1084,7 +271,10 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
 
     SolveLaunch L{ctx, has_s, ncta, n_rows, n_panels, stream, profile_reps, ms};
     L.pd = p;
-    if (!dispatch_tbw(L, mixed, b, W)) return set_error(ctx, TB_ERR_UNSUPPORTED, "no solver variant for W=%d", W);
+    const bool launched = opts.precision == TB_PREC_FP64    ? launch_panel_f64(L, b, W)
+                          : opts.precision == TB_PREC_MIXED ? launch_panel_f32(L, b, W)
+                                                            : launch_panel_df(L, b, W);
+    if (!launched) return set_error(ctx, TB_ERR_UNSUPPORTED, "no solver variant for W=%d", W);
     if (L.rc) return L.rc;
     TB_CUDA_TRY(ctx, cudaGetLastError());
     if (profiling) return TB_OK;

@@ -154,6 +154,37 @@ struct Acc<float> {
     }
 };
 
+// df values accumulate like FP32 two-float sums (hi by TwoSum, lo added).
+template <>
+struct Acc<df> {
+    float hi, lo;
+    typedef float2 P;
+    __device__ __forceinline__ void zero() { hi = lo = 0.f; }
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x;
+        const float bb = s - hi;
+        const float e = (hi - (s - bb)) + (x - bb);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ void add(df x) {
+        add(x.hi);
+        lo += x.lo;
+    }
+    __device__ __forceinline__ void add(const Acc &o) {
+        add(o.hi);
+        lo += o.lo;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ P pack() const { return make_float2(hi, lo); }
+    __device__ __forceinline__ static Acc unpack(P p) {
+        Acc a;
+        a.hi = p.x;
+        a.lo = p.y;
+        return a;
+    }
+};
+
 // Sums per-thread accumulators acc[CPT][K] over the CTA per column and writes
 // the CTA partials to part[(c*K + k) * gridDim.x + blockIdx.x].
 template <typename T, int W, int NT, int K>
@@ -179,6 +210,17 @@ __device__ __forceinline__ void cta_partials(Acc<T> (&acc)[PanelVec<T>::CPT][K],
 
 // Warp-wide sum of an accumulator (two-float for FP32: no FP64 instructions).
 __device__ __forceinline__ void warp_reduce(Acc<double> &s) { s.s = warp_sum(s.s); }
+template <typename A>
+__device__ __forceinline__ void warp_reduce_pair(A &s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        A t;
+        t.hi = __shfl_xor_sync(TB_FULL_MASK, s.hi, o);
+        t.lo = __shfl_xor_sync(TB_FULL_MASK, s.lo, o);
+        s.add(t);
+    }
+}
+__device__ __forceinline__ void warp_reduce(Acc<df> &s) { warp_reduce_pair(s); }
 __device__ __forceinline__ void warp_reduce(Acc<float> &s) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

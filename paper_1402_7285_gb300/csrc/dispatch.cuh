@@ -45,5 +45,7 @@ bool dispatch_tbw(F &f, bool f32, int b, int W) {
 }
 
 void launch_to_float(const double *src, float *dst, int64_t n, cudaStream_t s);
+// FP64 matrix values -> the precision's value type (FP32 or df) in dst
+void convert_values(int precision, const double *src, void *dst, int64_t n, cudaStream_t s);
 
 } // namespace tbgf

@@ -29,7 +29,7 @@ __global__ void k_pad_in(const double *__restrict__ src, int ncols, T *__restric
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = t / W;
         const int c = (int)(t % W);
-        T re = 0, im = 0;
+        T re = (T)0, im = (T)0;
         if (c < ncols) {
             re = (T)src[(r * ncols + c) * 2];
             im = (T)src[(r * ncols + c) * 2 + 1];
@@ -53,6 +53,11 @@ __global__ void k_unpad_out(const T *__restrict__ src, int W, double *__restrict
 __global__ void k_to_float(const double *__restrict__ src, float *__restrict__ dst, int64_t n) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         dst[t] = (float)src[t];
+}
+
+__global__ void k_to_df(const double *__restrict__ src, df *__restrict__ dst, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = df(src[t]);
 }
 
 struct SpmmLaunch {
@@ -83,6 +88,17 @@ void launch_to_float(const double *src, float *dst, int64_t n, cudaStream_t s) {
     if (g < 1) g = 1;
     k_to_float<<<g, 256, 0, s>>>(src, dst, n);
 }
+void launch_to_df(const double *src, void *dst, int64_t n, cudaStream_t s) {
+    int g = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    if (g < 1) g = 1;
+    k_to_df<<<g, 256, 0, s>>>(src, (df *)dst, n);
+}
+void convert_values(int precision, const double *src, void *dst, int64_t n, cudaStream_t s) {
+    if (precision == TB_PREC_MIXED)
+        launch_to_float(src, (float *)dst, n, s);
+    else if (precision == TB_PREC_DF64)
+        launch_to_df(src, dst, n, s);
+}
 } // namespace tbgf
 
 extern "C" int tb_bsr_spmm(tb_ctx *ctx, const tb_bsr *A, const double *X, int32_t ncols, double *Y,
@@ -91,7 +107,8 @@ extern "C" int tb_bsr_spmm(tb_ctx *ctx, const tb_bsr *A, const double *X, int32_
     if (!ctx) return TB_ERR_ARG;
     TB_CHECK(ctx, A && A->row_ptr && A->col_idx && A->val, TB_ERR_ARG, "tb_bsr_spmm: matrix arrays missing");
     TB_CHECK(ctx, X && Y && ncols >= 1 && ncols <= 64, TB_ERR_ARG, "tb_bsr_spmm: ncols must be 1..64");
-    TB_CHECK(ctx, precision == TB_PREC_FP64 || precision == TB_PREC_MIXED, TB_ERR_ARG, "bad precision");
+    TB_CHECK(ctx, precision == TB_PREC_FP64 || precision == TB_PREC_MIXED || precision == TB_PREC_DF64, TB_ERR_ARG,
+             "bad precision");
     TB_CHECK(ctx, supported_bdim(A->bdim), TB_ERR_UNSUPPORTED, "tb_bsr_spmm: bdim %d not built", A->bdim);
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = A->n_brows * A->bdim;
@@ -108,28 +125,34 @@ extern "C" int tb_bsr_spmm(tb_ctx *ctx, const tb_bsr *A, const double *X, int32_
     rc = validate_bsr(ctx, (const int64_t *)rp, (const int32_t *)ci, val, A->n_brows, A->nnzb, s, "A");
     if (rc) return rc;
     const int W = panel_width_for(ncols);
-    const bool f32 = precision == TB_PREC_MIXED;
+    const bool f32 = precision == TB_PREC_MIXED, dfp = precision == TB_PREC_DF64;
     const size_t esz = f32 ? 4 : 8;
-    size_t off_val = 0, off_x = f32 ? align_up(sizeof(float) * A->nnzb * bb, 256) : 0;
+    size_t off_val = 0, off_x = (f32 || dfp) ? align_up(esz * A->nnzb * bb, 256) : 0;
     size_t off_y = off_x + align_up(esz * 2 * n * W, 256);
     void *wsp;
     rc = ws_get(ctx, WS_SPMM_STAGE, off_y + esz * 2 * n * W, &wsp);
     if (rc) return rc;
     char *ws = (char *)wsp;
     const void *mval = val;
-    if (f32) {
-        launch_to_float((const double *)val, (float *)(ws + off_val), A->nnzb * bb, s);
+    if (f32 || dfp) {
+        convert_values(precision, (const double *)val, ws + off_val, A->nnzb * bb, s);
         mval = ws + off_val;
     }
     int g = (int)std::min<int64_t>((n * W + 255) / 256, 152 * 16);
     if (f32)
         k_pad_in<float><<<g, 256, 0, s>>>((const double *)x, ncols, (float *)(ws + off_x), W, n);
+    else if (dfp)
+        k_pad_in<df><<<g, 256, 0, s>>>((const double *)x, ncols, (df *)(ws + off_x), W, n);
     else
         k_pad_in<double><<<g, 256, 0, s>>>((const double *)x, ncols, (double *)(ws + off_x), W, n);
     SpmmLaunch L{(const int64_t *)rp, (const int32_t *)ci, mval, A->n_brows, ws + off_x, ws + off_y, s, 152 * 8};
-    if (!dispatch_tbw(L, f32, A->bdim, W)) return set_error(ctx, TB_ERR_UNSUPPORTED, "no SpMM variant");
+    const bool ok = f32 ? dispatch_bw<float>(L, A->bdim, W) : dfp ? dispatch_bw<df>(L, A->bdim, W)
+                                                             : dispatch_bw<double>(L, A->bdim, W);
+    if (!ok) return set_error(ctx, TB_ERR_UNSUPPORTED, "no SpMM variant");
     if (f32)
         k_unpad_out<float><<<g, 256, 0, s>>>((const float *)(ws + off_y), W, (double *)y, ncols, n);
+    else if (dfp)
+        k_unpad_out<df><<<g, 256, 0, s>>>((const df *)(ws + off_y), W, (double *)y, ncols, n);
     else
         k_unpad_out<double><<<g, 256, 0, s>>>((const double *)(ws + off_y), W, (double *)y, ncols, n);
     TB_CUDA_TRY(ctx, cudaGetLastError());

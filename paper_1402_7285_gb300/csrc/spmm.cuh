@@ -10,7 +10,10 @@
 // panel's type T.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
+#include "df64.cuh"
 
 template <typename T>
 struct PanelVec;
@@ -24,6 +27,12 @@ struct PanelVec<double> {
     typedef double2 V;
     static constexpr int CPT = 1;
 };
+// one complex df (re.hi, re.lo, im.hi, im.lo) per 16-byte vector
+template <>
+struct PanelVec<df> {
+    typedef float4 V;
+    static constexpr int CPT = 1;
+};
 
 // load / store CPT complex values of one panel row for lane `lane`
 template <typename T, int W>
@@ -31,7 +40,9 @@ __device__ __forceinline__ void ld_row(const T *__restrict__ base, int64_t row, 
                                        cpx<T> (&x)[PanelVec<T>::CPT]) {
     typedef typename PanelVec<T>::V V;
     const V v = *reinterpret_cast<const V *>(base + (row * W + (int64_t)lane * PanelVec<T>::CPT) * 2);
-    if constexpr (PanelVec<T>::CPT == 2) {
+    if constexpr (std::is_same<T, df>::value) {
+        x[0] = mk(df(v.x, v.y), df(v.z, v.w));
+    } else if constexpr (PanelVec<T>::CPT == 2) {
         x[0] = mk(v.x, v.y);
         x[1] = mk(v.z, v.w);
     } else {
@@ -44,7 +55,9 @@ __device__ __forceinline__ void st_row(T *__restrict__ base, int64_t row, int la
                                        const cpx<T> (&x)[PanelVec<T>::CPT]) {
     typedef typename PanelVec<T>::V V;
     V v;
-    if constexpr (PanelVec<T>::CPT == 2) {
+    if constexpr (std::is_same<T, df>::value) {
+        v.x = x[0].re.hi, v.y = x[0].re.lo, v.z = x[0].im.hi, v.w = x[0].im.lo;
+    } else if constexpr (PanelVec<T>::CPT == 2) {
         v.x = x[0].re, v.y = x[0].im, v.z = x[1].re, v.w = x[1].im;
     } else {
         v.x = x[0].re, v.y = x[0].im;
@@ -55,7 +68,13 @@ __device__ __forceinline__ void st_row(T *__restrict__ base, int64_t row, int la
 // Read the B x B block at `blk` into registers (vector loads when aligned).
 template <typename T, int B>
 __device__ __forceinline__ void ld_block(const T *__restrict__ blk, T (&a)[B * B]) {
-    if constexpr ((B * B * sizeof(T)) % 16 == 0) {
+    if constexpr (std::is_same<T, df>::value && (B * B * sizeof(T)) % 16 == 0) {
+#pragma unroll
+        for (int q = 0; q < B * B / 2; ++q) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(blk) + q);
+            a[2 * q] = df(v.x, v.y), a[2 * q + 1] = df(v.z, v.w);
+        }
+    } else if constexpr ((B * B * sizeof(T)) % 16 == 0) {
         constexpr int PER = 16 / sizeof(T);
 #pragma unroll
         for (int q = 0; q < B * B / PER; ++q) {
@@ -69,7 +88,7 @@ __device__ __forceinline__ void ld_block(const T *__restrict__ blk, T (&a)[B * B
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < B * B; ++q) a[q] = __ldg(blk + q);
+        for (int q = 0; q < B * B; ++q) a[q] = ldg_val(blk + q);
     }
 }
 

@@ -104,6 +104,18 @@ def test_local_fp64_matches_oracle(ctx, spec, radii):
         assert rel_err_per_shift(g, ref_lu[c]).max() < 1e-10
 
 
+def test_local_df64_matches_oracle(ctx):
+    o, rows, rad, sptr, satoms, rl, optr, orows = _local_case(scaled(C5_SYSTEM, L=12), 16, (2, 3))
+    z = midpoint_shifts(10, -8.0, 8.0, 0.05)
+    res = tb.solve_local(ctx, _bsr(o.H), _bsr(o.S), z, rows, sptr, satoms, optr, orows, tol=1e-11,
+                         precision=tb.TB_PREC_DF64)
+    assert np.all(_np(res.status) == tb.TB_COL_CONVERGED)
+    G = _np(res.G)
+    _, ref_lu = _oracle_local(o, rows, sptr, satoms, rl, z, 1e-12)
+    for c in range(len(rows)):
+        assert rel_err_per_shift(G[optr[c]:optr[c + 1]], ref_lu[c]).max() < 1e-9
+
+
 def test_local_order_does_not_change_results(ctx):
     o, rows, rad, sptr, satoms, rl, optr, orows = _local_case(scaled(C5_SYSTEM, L=10), 30, (1, 2, 3))
     z = midpoint_shifts(6, -8.0, 6.0, 0.1)
