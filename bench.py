@@ -190,14 +190,15 @@ def run_ours(args, rank, world):
     wt = torch.as_tensor(w_q, device=dev)
     if args.kernel_profile:
         cols, ptr, orows = dev_panel(0)
-        prof = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W)
+        prof = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W,
+                          ctas_per_sm=args.ctas_per_sm)
         torch.cuda.synchronize()
         ctx.close()
         return {"kernel_profile": prof}
 
     def step_device(cols, ptr, orows):
         r = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=prec, panel_w=W,
-                     max_iter=args.max_iter)
+                     max_iter=args.max_iter, ctas_per_sm=args.ctas_per_sm)
         L, D = tb.reduce_ldos_dm(ctx, r.G, zt, wt, mu, kT, cols, ptr, orows, S=S)
         return r
 
@@ -259,7 +260,7 @@ def run_ours(args, rank, world):
         e2e_pairs, h2d_b, d2h_b = 0, 0, 0
         for cols, ptr, orows in host_panels:
             r = tb.solve(ctx, Hp, Sp, zp, cols, ptr, orows, tol=WORKLOAD.tol, precision=prec, panel_w=W,
-                         max_iter=args.max_iter)
+                         max_iter=args.max_iter, ctas_per_sm=args.ctas_per_sm)
             L, D = tb.reduce_ldos_dm(ctx, r.G, zp, wp, mu, kT, cols, ptr, orows, S=Sp)
             e2e_pairs += int((r.resid <= WORKLOAD.tol).sum())
             h2d_b += h2d + sum(int(a.numel() * a.element_size()) for a in (cols, ptr, orows)) * 2
@@ -279,7 +280,8 @@ def run_ours(args, rank, world):
 
     # ---- roofline of the dominant kernel (CUDA events on this stream)
     cols, ptr, orows = panels[0]
-    prof = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W)
+    prof = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W,
+                      ctas_per_sm=args.ctas_per_sm)
     counts = {"A_outer_H_product": outer, "B_update": outer, "IC_A_inner_S_product": inner,
               "IC_B_inner_update": inner, "C_rho": outer}
     share = {k: prof[k] * counts[k] for k in prof}
@@ -341,11 +343,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--panel-w", type=int, default=64)
+    ap.add_argument("--panel-w", type=int, default=16)
     ap.add_argument("--precision", default="df64", choices=["df64", "mixed", "fp64"])
     ap.add_argument("--kernel-profile", action="store_true",
                     help="only launch the solver kernels of one panel (CUDA events; for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=100000)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--profile-reps", type=int, default=10)

@@ -160,10 +160,11 @@ typedef struct {
     int32_t precision;   /* TB_PREC_FP64 (default), TB_PREC_MIXED or TB_PREC_DF64 */
     int32_t panel_w;     /* columns solved together; 0 = autotuned                */
     int32_t seed_shift;  /* index of the seed shift; -1 = median Re z (default)    */
-    double inner_tol;    /* S != I: relative tolerance of the inner CG on S;
-                            0 = default (1e-13 FP64, 1e-12 DF64, 1e-7 mixed)      */
+    double inner_tol;    /* S != I: relative tolerance of the inner CG on S; 0 =
+                            max(1e-3 tol, floor), floor 1e-13 FP64, 1e-12 DF64,
+                            1e-7 mixed                                            */
     int32_t inner_max;   /* S != I: inner iterations per outer iteration, 0 = 40   */
-    int32_t reserved0;
+    int32_t ctas_per_sm; /* resident CTAs per SM for the panel kernels, 0 = auto  */
     void *stream;        /* cudaStream_t to queue work on                         */
     int64_t *stats;      /* optional host array [2]: outer and inner iterations
                             summed over all panels (written before returning)     */

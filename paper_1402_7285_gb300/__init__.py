@@ -235,7 +235,7 @@ class SolveResult:
 
 def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_rows, *, tol=1e-10,
           max_iter=100000, precision=TB_PREC_FP64, panel_w=0, seed_shift=-1, inner_tol=0.0, inner_max=0,
-          outputs_like=None) -> SolveResult:
+          outputs_like=None, ctas_per_sm=0) -> SolveResult:
     """G[(out_row_ptr[c] + k), m] = e_i^T (z_m S - H)^{-1} e_j, i = out_rows[...], j = rhs_rows[c]."""
     like = H.val if outputs_like is None else outputs_like
     zc = _as(z, np.complex128, like=like)
@@ -250,7 +250,8 @@ def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_
     resid = _empty((n_rhs, n_z), np.float64, like)
     status = _empty((n_rhs,), np.int32, like)
     stats = np.zeros(2, np.int64)
-    opts = _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, _stream_of(like), stats)
+    opts = _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, _stream_of(like), stats,
+                 ctas_per_sm)
     Hc = H.c_struct()
     Sc = S.c_struct() if S is not None else None
     rc = ctx.lib.shifted_cocg_solve(ctx.h, ctypes.byref(Hc), ctypes.byref(Sc) if Sc is not None else None,
@@ -260,9 +261,10 @@ def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_
     return SolveResult(G, iters, resid, status, rc, int(stats[0]), int(stats[1]))
 
 
-def _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, stream, stats):
+def _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, stream, stats, ctas_per_sm=0):
     opts = _lib.TbSolveOpts()
     ctx.lib.tb_solve_opts_default(ctypes.byref(opts))
+    opts.ctas_per_sm = ctas_per_sm
     opts.tol, opts.max_iter, opts.precision, opts.panel_w = tol, max_iter, precision, panel_w
     opts.seed_shift, opts.inner_tol, opts.inner_max = seed_shift, inner_tol, inner_max
     opts.stream = stream
@@ -274,14 +276,14 @@ PROFILE_KERNELS = ("A_outer_H_product", "B_update", "IC_A_inner_S_product", "IC_
 
 
 def profile(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_rows, *, reps=20,
-            precision=TB_PREC_FP64, panel_w=0, seed_shift=-1, tol=1e-10) -> dict:
+            precision=TB_PREC_FP64, panel_w=0, seed_shift=-1, tol=1e-10, ctas_per_sm=0) -> dict:
     """Average ms per launch of each solver kernel (CUDA events; shifted_cocg_profile)."""
     like = H.val
     zc = _as(z, np.complex128, like=like)
     rhs = _as(rhs_rows, np.int64, like=like)
     optr = _as(out_row_ptr, np.int64, like=like)
     orows = _as(out_rows, np.int64, like=like)
-    opts = _opts(ctx, tol, 100000, precision, panel_w, seed_shift, 0.0, 0, _stream_of(like), None)
+    opts = _opts(ctx, tol, 100000, precision, panel_w, seed_shift, 0.0, 0, _stream_of(like), None, ctas_per_sm)
     ms = np.zeros(8, np.float64)
     Hc = H.c_struct()
     Sc = S.c_struct() if S is not None else None

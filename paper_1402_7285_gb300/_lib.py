@@ -43,7 +43,7 @@ class TbSolveOpts(ctypes.Structure):
     _fields_ = [
         ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("panel_w", ctypes.c_int32), ("seed_shift", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-        ("inner_max", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("inner_max", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("stats", ctypes.c_void_p),
     ]
 

@@ -159,7 +159,9 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const size_t vec_bytes = align_up(esz * 2 * n_rows * W, 256);
     const int n_vec = has_s ? 11 : 4;
     const int per_cta = NT / (W / (mixed ? 2 : 1));
-    int ncta = (int)std::min<int64_t>((int64_t)2 * num_sms(), (H->n_brows + per_cta - 1) / per_cta);
+    TB_CHECK(ctx, opts.ctas_per_sm >= 0 && opts.ctas_per_sm <= 8, TB_ERR_ARG, "ctas_per_sm must be 0..8");
+    const int per_sm = opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 3;
+    int ncta = (int)std::min<int64_t>((int64_t)per_sm * num_sms(), (H->n_brows + per_cta - 1) / per_cta);
     if (ncta < 1) ncta = 1;
     void *vec_base = nullptr;
     rc = ws_get(ctx, WS_SOLVE_VEC, vec_bytes * n_vec, &vec_base);
@@ -259,7 +261,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.part = sb + o_part;
     p.ctl = (Ctrl *)(sb + o_ctl);
     p.tol = opts.tol;
-    p.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : (mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13));
+    p.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : std::max(1e-3 * opts.tol, mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13));
     p.max_iter = opts.max_iter;
     p.inner_max = opts.inner_max > 0 ? opts.inner_max : 40;
     p.outer_cap = opts.max_iter + 2;

@@ -207,7 +207,7 @@ extern "C" int shifted_cocg_solve_local(tb_ctx *ctx, const tb_bsr *H, const tb_b
     la.queue = (unsigned long long *)(ws + o_q);
     la.stat = (unsigned long long *)(ws + o_q) + 1;
     la.tol = opts.tol;
-    la.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : (mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13));
+    la.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : std::max(1e-3 * opts.tol, mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13));
     la.max_iter = opts.max_iter;
     la.inner_max = opts.inner_max > 0 ? opts.inner_max : 40;
     la.G = (c64 *)d_G;

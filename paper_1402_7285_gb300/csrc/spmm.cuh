@@ -104,6 +104,8 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
 #pragma unroll
         for (int c = 0; c < CPT; ++c) acc[i][c] = mk<T>(0, 0);
     const int64_t k0 = __ldg(rp + br), k1 = __ldg(rp + br + 1);
+    // two blocks per trip keep twice the neighbour loads in flight
+#pragma unroll 2
     for (int64_t k = k0; k < k1; ++k) {
         const int64_t col = __ldg(ci + k);
         cpx<T> x[B][CPT];

@@ -95,3 +95,61 @@ def test_mlp_predict_and_train_track_oracle(ctx):
             opt.step(po, mlp.backward(po, X[s:s + 128].astype(np.float64), t[s:s + 128].astype(np.float64)))
     lo = mlp.loss(po, X.astype(np.float64), t.astype(np.float64))
     assert abs(hist[-1] - lo) < 0.25 * lo + 1e-3
+
+
+def test_learned_order_gains_over_plain_order(ctx):
+    """Train the predictor on solver-generated (descriptor, iterations) pairs of
+    one set of columns, order a held-out set longest-predicted-first, and
+    compare the list-scheduling makespan over the solver's CTAs with the plain
+    (given) order, using the measured per-column costs."""
+    import time
+    from paper_1402_7285_gb300 import scheduler
+    from workloads import midpoint_shifts
+    spec = scaled(C4_SYSTEM, n_sites=40000)
+    Hh, Sh, _ = tb.build_system(spec, 1234)
+    Hd, Sd = Hh.to(DEV), Sh.to(DEV)
+    rows, rad = sample_local_rhs(Hh.n_brows, spec.bdim, 2400, (1, 2, 3, 4), 99)
+    perm = np.random.default_rng(5).permutation(len(rows))     # plain order is arbitrary w.r.t. cost
+    rows, rad = rows[perm], rad[perm]
+    sptr, satoms = tb.local_subspaces(Hh, rows, rad)
+    D = _np(tb.descriptors(ctx, Hd, Sd, rows, rad, sptr, satoms))
+    optr = np.arange(len(rows) + 1, dtype=np.int64)
+    z = midpoint_shifts(16, -8.0, 8.0, 0.01)
+    res = tb.solve_local(ctx, Hd, Sd, z, rows, sptr, satoms, optr, rows, tol=1e-6, precision=tb.TB_PREC_DF64)
+    assert np.all(_np(res.status) == tb.TB_COL_CONVERGED)
+    iters = _np(res.iters).astype(np.float64)
+    n_tr = 1600
+    pred_model, hist = scheduler.train(ctx, D[:n_tr], iters[:n_tr], epochs=80, batch=128, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    test = slice(n_tr, len(rows))
+    p_it = scheduler.predict(ctx, pred_model, D[test])
+    true_it = iters[test]
+    # rank correlation between predicted and true iteration counts
+    rk = lambda a: np.argsort(np.argsort(a))
+    rho = np.corrcoef(rk(p_it), rk(true_it))[0, 1]
+    assert rho > 0.6, rho
+    size = np.diff(sptr)[test] * spec.bdim
+    cost = true_it * size                   # work per column ~ iterations x subspace rows
+    workers = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    plain = scheduler.greedy_makespan(cost, np.arange(len(cost)), workers)
+    learned = scheduler.greedy_makespan(cost, scheduler.longest_first(p_it * size), workers)
+    best = scheduler.greedy_makespan(cost, scheduler.longest_first(cost), workers)
+    assert learned <= plain
+    print(f"makespan plain {plain:.3e} learned {learned:.3e} exact-order {best:.3e} "
+          f"(gain {plain / learned:.3f}); rank corr {rho:.3f}")
+    # the same comparison on the GPU: solve the held-out columns in both orders
+    sub = lambda a: a[test]
+    tp = np.concatenate([[0], np.cumsum(np.diff(sptr)[test])]).astype(np.int64)
+    ta = np.concatenate([satoms[sptr[c]:sptr[c + 1]] for c in range(n_tr, len(rows))])
+    op = np.arange(len(true_it) + 1, dtype=np.int64)
+    times = {}
+    for name, order in (("plain", None), ("learned", scheduler.longest_first(p_it * size))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = tb.solve_local(ctx, Hd, Sd, z, sub(rows), tp, ta, op, sub(rows), order=order, tol=1e-6,
+                           precision=tb.TB_PREC_DF64)
+        torch.cuda.synchronize()
+        times[name] = time.perf_counter() - t0
+        assert np.array_equal(_np(r.iters), true_it.astype(np.int32))
+    print(f"GPU time plain {times['plain']:.3f}s learned {times['learned']:.3f}s")
+    assert times["learned"] <= 1.05 * times["plain"]
