@@ -105,7 +105,9 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     std::vector<int64_t> pan_row((size_t)n_panels * W, -1), pan_dst((size_t)n_panels * W, -1);
     std::vector<int32_t> pan_eptr((size_t)n_panels * (W + 1), 0);
     std::vector<int64_t> pan_ebase(n_panels, 0);
-    int64_t max_ent = 1;
+    int64_t max_ent = 1, max_col_ent = 1;
+    for (int64_t c = 0; c < n_rhs; ++c) max_col_ent = std::max<int64_t>(max_col_ent, h_optr[c + 1] - h_optr[c]);
+    TB_CHECK(ctx, max_col_ent < (1 << 24), TB_ERR_SIZE, "too many kept rows in one column");
     for (int pnl = 0; pnl < n_panels; ++pnl) {
         const int64_t c0 = (int64_t)pnl * W;
         pan_ebase[pnl] = h_optr[c0];
@@ -250,6 +252,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.zs = mk(h_z[2 * seed], h_z[2 * seed + 1]);
     p.z = (const c64 *)(sb + o_zc);
     p.max_ent = (int32_t)max_ent;
+    p.max_col_ent = (int32_t)max_col_ent;
     p.xs = (c64 *)proj_base;
     p.ps = (c64 *)proj_base + max_ent * n_z;
     p.pan_row = (const int64_t *)(sb + o_prow);

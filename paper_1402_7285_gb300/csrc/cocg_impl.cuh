@@ -93,72 +93,117 @@ __global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
 }
 
 // ------------------------------------------------------------ shifted steps
-// A(n): rotate pi, test ||rt_n|| / |pi_n| <= tol, then p^m_n on the kept rows.
+// The (slot, shift) pairs are split into contiguous ranges, one per CTA.  Each
+// range is processed in chunks: phase 1, one thread per pair, runs the FP64
+// shifted recurrence and leaves two coefficients in shared memory; phase 2
+// spreads the (pair, kept row) updates over all threads of the CTA, so the
+// kept rows of a column are updated in parallel, not one after another.
+constexpr int PAIR_CHUNK = 128;
+
+// A(n): rotate pi, test ||rt_n|| / |pi_n| <= tol, then p^m_n = r_n / pi_n + beta^m_{n-1} p^m_{n-1}.
 template <typename T, int W>
 __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) {
+    __shared__ c64 s_a[PAIR_CHUNK], s_b[PAIR_CHUNK];
+    __shared__ int s_c[PAIR_CHUNK], s_m[PAIR_CHUNK], s_on[PAIR_CHUNK];
     const int panel = p.ctl->panel;
     const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
     const int64_t ebase = p.pan_ent_base[panel];
-    const int pairs = W * p.nz;
-    for (int q = (int)spread_index(); q < pairs; q += gridDim.x * blockDim.x) {
-        const int c = q / p.nz, m = q % p.nz;
-        ColState &C = p.col[c];
-        if (C.done) continue;
-        ShiftState &S = p.sh[q];
-        if (!S.active) continue;
-        S.pi_prev = S.pi;
-        S.pi = S.pi_next;
-        const double res = sqrt(C.rn2) / sqrt(cabs2(S.pi));
-        S.resid = res;
-        if (res <= p.tol) {
-            S.active = 0;
-            S.conv_it = n;
-            atomicSub(&C.n_active, 1);
-            continue;
+    const int P = W * p.nz;
+    const int q0 = (int)((int64_t)blockIdx.x * P / gridDim.x), q1 = (int)((int64_t)(blockIdx.x + 1) * P / gridDim.x);
+    const int KM = p.max_col_ent;
+    for (int base = q0; base < q1; base += PAIR_CHUNK) {
+        const int np = min(PAIR_CHUNK, q1 - base);
+        for (int t = threadIdx.x; t < np; t += blockDim.x) {
+            const int q = base + t, c = q / p.nz, m = q % p.nz;
+            int on = 0;
+            ColState &C = p.col[c];
+            ShiftState &S = p.sh[q];
+            if (!C.done && S.active) {
+                S.pi_prev = S.pi;
+                S.pi = S.pi_next;
+                const double res = sqrt(C.rn2) / sqrt(cabs2(S.pi));
+                S.resid = res;
+                if (res <= p.tol) {
+                    S.active = 0;
+                    S.conv_it = n;
+                    atomicSub(&C.n_active, 1);
+                } else {
+                    const c64 ratio = cdiv(S.pi_prev, S.pi);
+                    s_b[t] = (ratio * ratio) * C.beta_prev;
+                    s_a[t] = cdiv(mk(1.0, 0.0), S.pi);
+                    on = 1;
+                }
+            }
+            s_on[t] = on;
+            s_c[t] = c;
+            s_m[t] = m;
         }
-        const c64 ratio = cdiv(S.pi_prev, S.pi);
-        const c64 bs = (ratio * ratio) * C.beta_prev;
-        const c64 ipi = cdiv(mk(1.0, 0.0), S.pi);
-        for (int e = eptr[c]; e < eptr[c + 1]; ++e) {
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < (int64_t)np * KM; i += blockDim.x) {
+            const int t = (int)(i / KM), k = (int)(i % KM);
+            if (!s_on[t]) continue;
+            const int c = s_c[t], m = s_m[t];
+            const int e = eptr[c] + k;
+            if (e >= eptr[c + 1]) continue;
             const int64_t row = p.ent_row[ebase + e];
             const T *rp = Rc + (row * W + c) * 2;
             const c64 rv = mk((double)rp[0], (double)rp[1]);
             c64 *ps = p.ps + (int64_t)e * p.nz + m;
-            *ps = ipi * rv + bs * (*ps);
+            *ps = s_a[t] * rv + s_b[t] * (*ps);
         }
+        __syncthreads();
     }
 }
 
 // B(n) / B'(n): pi_{n+1}, alpha^m_n and x^m += alpha^m_n p^m_n on the kept rows.
 template <typename T, int W>
 __device__ void pair_step_B(const Panel<T> &p) {
+    __shared__ c64 s_a[PAIR_CHUNK];
+    __shared__ int s_c[PAIR_CHUNK], s_m[PAIR_CHUNK], s_on[PAIR_CHUNK];
     const int panel = p.ctl->panel;
     const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
-    const int pairs = W * p.nz;
-    for (int q = (int)spread_index(); q < pairs; q += gridDim.x * blockDim.x) {
-        const int c = q / p.nz, m = q % p.nz;
-        ColState &C = p.col[c];
-        if (C.done) continue;
-        ShiftState &S = p.sh[q];
-        if (!S.active) continue;
-        const c64 sig = p.z[m] - p.zs;
-        const c64 coef = cdiv(C.alpha * C.beta_prev, C.alpha_prev);
-        const c64 one = mk(1.0, 0.0);
-        const c64 pn = (one + C.alpha * sig) * S.pi + coef * (S.pi - S.pi_prev);
-        const c64 as = cdiv(S.pi, pn) * C.alpha;
-        if (!cfinite(pn) || (pn.re == 0.0 && pn.im == 0.0) || !cfinite(as)) {
-            S.active = 0;
-            S.resid = nan("");
-            C.breakdown = 1;
-            atomicSub(&C.n_active, 1);
-            continue;
+    const int P = W * p.nz;
+    const int q0 = (int)((int64_t)blockIdx.x * P / gridDim.x), q1 = (int)((int64_t)(blockIdx.x + 1) * P / gridDim.x);
+    const int KM = p.max_col_ent;
+    for (int base = q0; base < q1; base += PAIR_CHUNK) {
+        const int np = min(PAIR_CHUNK, q1 - base);
+        for (int t = threadIdx.x; t < np; t += blockDim.x) {
+            const int q = base + t, c = q / p.nz, m = q % p.nz;
+            int on = 0;
+            ColState &C = p.col[c];
+            ShiftState &S = p.sh[q];
+            if (!C.done && S.active) {
+                const c64 sig = p.z[m] - p.zs;
+                const c64 coef = cdiv(C.alpha * C.beta_prev, C.alpha_prev);
+                const c64 pn = (mk(1.0, 0.0) + C.alpha * sig) * S.pi + coef * (S.pi - S.pi_prev);
+                const c64 as = cdiv(S.pi, pn) * C.alpha;
+                if (!cfinite(pn) || (pn.re == 0.0 && pn.im == 0.0) || !cfinite(as)) {
+                    S.active = 0;
+                    S.resid = nan("");
+                    C.breakdown = 1;
+                    atomicSub(&C.n_active, 1);
+                } else {
+                    S.pi_next = pn;
+                    S.alpha_s = as;
+                    s_a[t] = as;
+                    on = 1;
+                }
+            }
+            s_on[t] = on;
+            s_c[t] = c;
+            s_m[t] = m;
         }
-        S.pi_next = pn;
-        S.alpha_s = as;
-        for (int e = eptr[c]; e < eptr[c + 1]; ++e) {
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < (int64_t)np * KM; i += blockDim.x) {
+            const int t = (int)(i / KM), k = (int)(i % KM);
+            if (!s_on[t]) continue;
+            const int c = s_c[t], m = s_m[t];
+            const int e = eptr[c] + k;
+            if (e >= eptr[c + 1]) continue;
             c64 *xs = p.xs + (int64_t)e * p.nz + m;
-            *xs = *xs + as * p.ps[(int64_t)e * p.nz + m];
+            *xs = *xs + s_a[t] * p.ps[(int64_t)e * p.nz + m];
         }
+        __syncthreads();
     }
 }
 
@@ -425,12 +470,12 @@ __global__ void __launch_bounds__(NT, 3) k_inner_a(Panel<T> p) {
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
     const int k = p.ctl->k;
     T *Dn = p.D[k & 1];
-    LdAxpy<T, W> ld; // d_k = t_k + beta d_{k-1}
+    LdAxpyReal<T, W> ld; // d_k = t_k + beta d_{k-1}, beta real
     ld.a = p.Tv;
     ld.b = (k == 0) ? nullptr : p.D[(k + 1) & 1];
     ld.lane = lane;
 #pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) ld.s[cc] = mk<T>((T)p.col[lane * CPT + cc].in_beta, 0);
+    for (int cc = 0; cc < CPT; ++cc) ld.s[cc] = (T)p.col[lane * CPT + cc].in_beta;
     Acc<T> acc[CPT][1];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero();
@@ -483,9 +528,9 @@ __global__ void __launch_bounds__(NT, 3) k_inner_b(Panel<T> p) {
     const int n = p.ctl->n;
     const T *D = p.D[k & 1];
     T *Y = p.R[(n + 1) & 1];
-    cpx<T> a[CPT];
+    T a[CPT]; // inner CG step length (real)
 #pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) a[cc] = mk<T>((T)p.col[lane * CPT + cc].in_alpha, 0);
+    for (int cc = 0; cc < CPT; ++cc) a[cc] = (T)p.col[lane * CPT + cc].in_alpha;
     Acc<T> acc[CPT][1];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero();

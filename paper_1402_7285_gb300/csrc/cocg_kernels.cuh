@@ -100,6 +100,7 @@ struct Panel {
     int32_t inner_max;
     int32_t outer_cap;
     int32_t in_graph; // 1: kernels run inside the solve graph and set its loop conditions
+    int32_t max_col_ent; // largest number of kept rows of one column
     // outputs (device)
     c64 *G;
     int32_t *iters;
@@ -268,6 +269,27 @@ struct LdAxpy {
             ld_row<T, W>(b, row, lane, y);
 #pragma unroll
             for (int c = 0; c < PanelVec<T>::CPT; ++c) x[c] = x[c] + s[c] * y[c];
+        }
+    }
+};
+
+// x = a(row) + s .* b(row) with real per-column scalars s
+template <typename T, int W>
+struct LdAxpyReal {
+    const T *a;
+    const T *b;
+    T s[PanelVec<T>::CPT];
+    int lane;
+    __device__ __forceinline__ void operator()(int64_t row, cpx<T> (&x)[PanelVec<T>::CPT]) const {
+        ld_row<T, W>(a, row, lane, x);
+        if (b) {
+            cpx<T> y[PanelVec<T>::CPT];
+            ld_row<T, W>(b, row, lane, y);
+#pragma unroll
+            for (int c = 0; c < PanelVec<T>::CPT; ++c) {
+                x[c].re = fma(s[c], y[c].re, x[c].re);
+                x[c].im = fma(s[c], y[c].im, x[c].im);
+            }
         }
     }
 };
