@@ -159,6 +159,7 @@ def run_ours(args, rank, world):
     import torch
 
     import paper_1402_7285_gb300 as tb
+    from paper_1402_7285_gb300 import sharding
 
     dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
     torch.cuda.set_device(dev)
@@ -175,7 +176,7 @@ def run_ours(args, rank, world):
     n_panels_total = len(rows_all) // W
 
     def panel(step):
-        k = (step * world + rank) % n_panels_total
+        k = sharding.panel_for(step, rank, world, n_panels_total)
         cols = rows_all[k * W:(k + 1) * W]
         ptr, orows = block_pattern_rows(Hh.row_ptr, Hh.col_idx, Hh.bdim, cols)
         return cols, ptr, orows
@@ -231,15 +232,7 @@ def run_ours(args, rank, world):
     outer = sum(r.outer_iters for r in results)
     inner = sum(r.inner_iters for r in results)
     launches = sum(13 + 3 * r.outer_iters + 2 * r.inner_iters for r in results)
-    t = torch.tensor([ms, pairs, launches], dtype=torch.float64, device=dev)
-    if world > 1:
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        ms_max, pairs_all, launches_all = float(mx[0]), float(sm[1]), float(sm[2])
-    else:
-        ms_max, pairs_all, launches_all = ms, float(pairs), float(launches)
+    ms_max, pairs_all, launches_all = sharding.reduce_step_stats(ms, float(pairs), float(launches), world, dev)
     value = pairs_all / (ms_max / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -268,13 +261,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         barrier()
         e2e_s = time.perf_counter() - t0
-        tt = torch.tensor([e2e_s, e2e_pairs], dtype=torch.float64, device=dev)
-        if world > 1:
-            mx = tt.clone()
-            torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-            sm = tt.clone()
-            torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-            e2e_s, e2e_pairs = float(mx[0]), float(sm[1])
+        e2e_s, e2e_pairs, _ = sharding.reduce_step_stats(e2e_s, float(e2e_pairs), 0.0, world, dev)
         e2e = {"value": e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d_b // e2e_steps,
                "d2h_bytes_per_step": d2h_b // e2e_steps, "steps": e2e_steps}
 
