@@ -155,6 +155,30 @@ def algorithmic_bytes(n_rows, nnzb, bdim, n_brows, W, n_z, n_ent, esz):
     }
 
 
+# FP32 instructions per df operation as implemented (csrc/df64.cuh): a lazily
+# accumulated product term 12, a normalised df fma 15, a df multiply 7, a df add 11.
+DF_TERM, DF_FMA, DF_MUL, DF_ADD = 12, 15, 7, 11
+FP32_PEAK_OPS = 152 * 128 * 2.07e9       # SMs x FP32 lanes x max SM clock (one op per lane per clock)
+
+
+def df_ops(n_rows, nnzb, bdim, W):
+    """FP32 instructions per launch of each solver kernel in df64 (complex panel of W)."""
+    bb = bdim * bdim
+    prod = nnzb * bb * W * 2 * DF_TERM                    # real block x complex panel, lazy sums
+    cx_axpy = 4 * DF_MUL + 4 * DF_ADD                     # x = a + s b, complex s (4 mul, 2+2 add)
+    re_axpy = 2 * DF_FMA                                  # x = a + s b, real s
+    nb_rows = nnzb * bdim * W                             # neighbour panel elements formed on the fly
+    own = n_rows * W
+    dot = 4 * DF_MUL + 4 * 8                              # complex product into two-float sums
+    return {
+        "A_outer_H_product": prod + nb_rows * cx_axpy + own * (2 * cx_axpy + 2 * DF_MUL + DF_ADD + dot),
+        "B_update": prod + nb_rows * cx_axpy + own * (2 * cx_axpy + 2 * DF_ADD + 2 * dot),
+        "IC_A_inner_S_product": prod + nb_rows * re_axpy + own * (re_axpy + dot),
+        "IC_B_inner_update": own * (4 * DF_FMA + dot),
+        "C_rho": own * dot,
+    }
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -265,6 +289,24 @@ def run_ours(args, rank, world):
         e2e = {"value": e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d_b // e2e_steps,
                "d2h_bytes_per_step": d2h_b // e2e_steps, "steps": e2e_steps}
 
+    # ---- the plain FP64 solver on the same panel (the comparison the metric names)
+    fp64 = None
+    if args.fp64_compare and prec != tb.TB_PREC_FP64:
+        cols, ptr, orows = panels[args.warmup]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r64 = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=tb.TB_PREC_FP64, panel_w=W,
+                       max_iter=args.max_iter, ctas_per_sm=args.ctas_per_sm)
+        tb.reduce_ldos_dm(ctx, r64.G, zt, wt, mu, kT, cols, ptr, orows, S=S)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        p64 = converged_pairs(r64)
+        fp64 = {"value": p64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64, "steps": 1,
+                "outer_iters": r64.outer_iters, "inner_iters": r64.inner_iters,
+                "note": "same panel as the first timed step, plain FP64 vectors and products"}
+
     # ---- roofline of the dominant kernel (CUDA events on this stream)
     cols, ptr, orows = panels[0]
     prof = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W,
@@ -278,15 +320,26 @@ def run_ours(args, rank, world):
     algo = algorithmic_bytes(Hh.n_rows, Hh.nnzb, Hh.bdim, Hh.n_brows, W, n_z, n_ent, esz)
     peaks = measured_peaks()
     achieved = algo[dom] / (prof[dom] * 1e-3) / 1e9
-    roof = {"bound": "alu" if prec == tb.TB_PREC_FP64 else "hbm", "kernel": dom, "achieved": achieved,
-            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-            "traffic": kernel_traffic(dom), "peak_source": peaks["source"] + " (burst, kernel timed alone)",
-            "bytes_per_launch": algo[dom], "ms_per_launch": prof[dom],
-            "per_kernel_ms": prof, "per_kernel_share": {k: share[k] / sum(share.values()) for k in share},
-            "per_kernel_gbs": {k: algo[k] / (prof[k] * 1e-3) / 1e9 for k in prof if prof[k] > 0}}
+    hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+           "peak_source": peaks["source"] + " (burst, kernel timed alone)", "bytes_per_launch": algo[dom]}
+    if prec == tb.TB_PREC_DF64:
+        # double-float products are bound by the FP32 pipes (ncu: FMA pipe ~50-60% active), not by HBM
+        ops = df_ops(Hh.n_rows, Hh.nnzb, Hh.bdim, W)
+        ach = ops[dom] / (prof[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_OPS / 1e12,
+                "unit": "TFLOP/s", "frac": ach / (FP32_PEAK_OPS / 1e12),
+                "op_definition": "FP32 operations of the df arithmetic as implemented, one per instruction; "
+                                 "peak = 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                "ops_per_launch": ops[dom], "traffic": kernel_traffic(dom), "hbm": hbm}
+    else:
+        roof = {"bound": "alu" if prec == tb.TB_PREC_FP64 else "hbm", "kernel": dom, **hbm,
+                "traffic": kernel_traffic(dom)}
+    roof.update({"ms_per_launch": prof[dom], "per_kernel_ms": prof,
+                 "per_kernel_share": {k: share[k] / sum(share.values()) for k in share},
+                 "per_kernel_gbs": {k: algo[k] / (prof[k] * 1e-3) / 1e9 for k in prof if prof[k] > 0}})
     ctx.close()
     return {"value": value, "ms": ms_max, "pairs": pairs_all, "launches": launches_all, "clocks": clk.summary(),
-            "e2e": e2e, "roofline": roof, "outer_iters": outer, "inner_iters": inner,
+            "e2e": e2e, "roofline": roof, "outer_iters": outer, "inner_iters": inner, "fp64": fp64,
             "iters_per_column": [int(x) for r in results for x in (r.iters.cpu().numpy() if hasattr(r.iters, "cpu")
                                                                     else r.iters)]}
 
@@ -336,6 +389,8 @@ def main():
                     help="only launch the solver kernels of one panel (CUDA events; for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=100000)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
+                    help="skip timing one panel with the plain FP64 solver")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--profile-reps", type=int, default=10)
@@ -394,7 +449,8 @@ def main():
             "clocks": out["clocks"], "e2e": out["e2e"], "gpu_launches": int(out["launches"]),
             "roofline": out["roofline"], "cpu_baseline": cpu,
             "solver": {"outer_iters": out["outer_iters"], "inner_iters": out["inner_iters"],
-                       "mean_iters_per_column": float(np.mean(out["iters_per_column"]))}}
+                       "mean_iters_per_column": float(np.mean(out["iters_per_column"]))},
+            "plain_fp64": out["fp64"]}
     print(json.dumps(line))
     if world > 1:
         import torch

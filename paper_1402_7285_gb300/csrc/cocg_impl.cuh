@@ -209,7 +209,7 @@ __device__ void pair_step_B(const Panel<T> &p) {
 
 // -------------------------------------------------------------- kernel A
 template <typename T, int B, int W, bool HAS_S>
-__global__ void __launch_bounds__(NT, 3) k_outer(Panel<T> p) {
+__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -336,7 +336,7 @@ __device__ void finish_outer(const Panel<T> &p, const double *rho_next, int init
 
 // -------------------------------------------------------------- kernel B (S = I)
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, 3) k_update_sI(Panel<T> p) {
+__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_sI(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(NT, 3) k_update_sI(Panel<T> p) {
 
 // -------------------------------------------------------------- kernel B' (S != I)
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, 3) k_update_S(Panel<T> p) {
+__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(NT, 3) k_update_S(Panel<T> p) {
 
 // ------------------------------------------------------- inner CG on S: IC_A
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, 3) k_inner_a(Panel<T> p) {
+__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_a(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(NT, 3) k_inner_a(Panel<T> p) {
 
 // ------------------------------------------------------- inner CG on S: IC_B
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, 3) k_inner_b(Panel<T> p) {
+__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(NT, 3) k_inner_b(Panel<T> p) {
 
 // -------------------------------------------------------------- kernel C (S != I)
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, 3) k_rho(Panel<T> p, int init) {
+__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_rho(Panel<T> p, int init) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;

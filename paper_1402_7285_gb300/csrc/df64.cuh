@@ -76,6 +76,25 @@ __host__ __device__ __forceinline__ df fma(df a, df b, df c) {
     return df_fast_two_sum(s.hi, DF_ADD(s.lo, DF_ADD(e, c.lo)));
 }
 
+// Lazy accumulator of a sum of products a_k b_k: the high parts of the
+// products are summed with TwoSum, everything below (product errors, cross
+// terms, TwoSum errors) in one plain FP32 sum; a single renormalisation at the
+// end.  12 FP32 operations per term instead of 15 for a normalised df fma.
+struct DfSum {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = c = 0.f; }
+    __device__ __forceinline__ void add_prod(df a, df b) {
+        const float p = DF_MUL(a.hi, b.hi);
+        float e = fmaf(a.hi, b.hi, -p);
+        e = fmaf(a.hi, b.lo, e);
+        e = fmaf(a.lo, b.hi, e);
+        const df t = df_two_sum(s, p);
+        s = t.hi;
+        c = DF_ADD(c, DF_ADD(t.lo, e));
+    }
+    __device__ __forceinline__ df value() const { return df_fast_two_sum(s, c); }
+};
+
 __device__ __forceinline__ df ldg_val(const df *p) {
     const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
     return df(v.x, v.y);

@@ -99,29 +99,53 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
                                                 const T *__restrict__ val, int64_t br, Loader &ld,
                                                 cpx<T> (&acc)[B][PanelVec<T>::CPT]) {
     constexpr int CPT = PanelVec<T>::CPT;
-#pragma unroll
-    for (int i = 0; i < B; ++i)
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[i][c] = mk<T>(0, 0);
     const int64_t k0 = __ldg(rp + br), k1 = __ldg(rp + br + 1);
-    // two blocks per trip keep twice the neighbour loads in flight
-#pragma unroll 2
-    for (int64_t k = k0; k < k1; ++k) {
-        const int64_t col = __ldg(ci + k);
-        cpx<T> x[B][CPT];
+    if constexpr (std::is_same<T, df>::value) {
+        DfSum sr[B], si[B];
 #pragma unroll
-        for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
-        T a[B * B];
-        ld_block<T, B>(val + k * (int64_t)(B * B), a);
+        for (int i = 0; i < B; ++i) sr[i].zero(), si[i].zero();
+#pragma unroll(B <= 4 ? 2 : 1)
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t col = __ldg(ci + k);
+            cpx<T> x[B][CPT];
+#pragma unroll
+            for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
+            T a[B * B];
+            ld_block<T, B>(val + k * (int64_t)(B * B), a);
+#pragma unroll
+            for (int i = 0; i < B; ++i)
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    sr[i].add_prod(a[i * B + j], x[j][0].re);
+                    si[i].add_prod(a[i * B + j], x[j][0].im);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) acc[i][0] = mk(sr[i].value(), si[i].value());
+    } else {
 #pragma unroll
         for (int i = 0; i < B; ++i)
 #pragma unroll
-            for (int j = 0; j < B; ++j)
+            for (int c = 0; c < CPT; ++c) acc[i][c] = mk<T>(0, 0);
+        // two blocks per trip keep twice the neighbour loads in flight (small blocks)
+#pragma unroll(B <= 4 ? 2 : 1)
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t col = __ldg(ci + k);
+            cpx<T> x[B][CPT];
 #pragma unroll
-                for (int c = 0; c < CPT; ++c) {
-                    acc[i][c].re = fma(a[i * B + j], x[j][c].re, acc[i][c].re);
-                    acc[i][c].im = fma(a[i * B + j], x[j][c].im, acc[i][c].im);
-                }
+            for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
+            T a[B * B];
+            ld_block<T, B>(val + k * (int64_t)(B * B), a);
+#pragma unroll
+            for (int i = 0; i < B; ++i)
+#pragma unroll
+                for (int j = 0; j < B; ++j)
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) {
+                        acc[i][c].re = fma(a[i * B + j], x[j][c].re, acc[i][c].re);
+                        acc[i][c].im = fma(a[i * B + j], x[j][c].im, acc[i][c].im);
+                    }
+        }
     }
 }
 
