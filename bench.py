@@ -127,15 +127,22 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def kernel_source_hash() -> str:
+    """sha256 over the sources of the solver kernels (the ncu figures are valid for these)."""
+    h = hashlib.sha256()
+    for f in ("cocg_impl.cuh", "cocg_kernels.cuh", "spmm.cuh", "df64.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1402_7285_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic(kernel: str) -> int | None:
     """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
-    path = os.path.join(ROOT, "profiles", "solver_kernels_c2_mixed_w64.md")
+    path = os.path.join(ROOT, "profiles", "solver_kernels_c2_df64_w16.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    src = open(os.path.join(ROOT, "paper_1402_7285_gb300", "csrc", "cocg.cu"), "rb").read()
-    if not m or m.group(1) != hashlib.sha256(src).hexdigest():
+    if not m or m.group(1) != kernel_source_hash():
         return None
     m = re.search(rf"traffic_bytes_per_launch\s+{re.escape(kernel)}\s*=\s*([0-9]+)", text)
     return int(m.group(1)) if m else None

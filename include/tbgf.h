@@ -158,7 +158,11 @@ typedef struct {
                             residual), default 1e-10                              */
     int32_t max_iter;    /* outer iterations, default 100000                        */
     int32_t precision;   /* TB_PREC_FP64 (default), TB_PREC_MIXED or TB_PREC_DF64 */
-    int32_t panel_w;     /* columns solved together; 0 = autotuned                */
+    int32_t panel_w;     /* columns solved together; 0 = autotuned: with >= 128
+                            columns the library times one iteration of its
+                            kernels for each width 8..64 and 2 or 3 CTAs per SM
+                            and keeps the fastest per column (cached per shape
+                            in the context); fewer columns use a heuristic     */
     int32_t seed_shift;  /* index of the seed shift; -1 = median Re z (default)    */
     double inner_tol;    /* S != I: relative tolerance of the inner CG on S; 0 =
                             max(1e-3 tol, floor), floor 1e-13 FP64, 1e-12 DF64,
@@ -201,7 +205,9 @@ int shifted_cocg_solve(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const doub
  * shifted_cocg_solve, no outputs).  After the panel is initialised, the
  * sequence  A, B, [IC_A, IC_B], C  (the bracketed pair and C only when
  * S != NULL) is launched `reps` times as ordinary launches on opts->stream,
- * each kernel bracketed by CUDA events.  ms[k] (k < 8) receives the average
+ * each kernel bracketed by CUDA events (with S, a first inner pair runs
+ * untimed before the timed one, so IC_A/IC_B are timed in their steady
+ * state with a previous search direction).  ms[k] (k < 8) receives the average
  * milliseconds per launch of kernel k: 0 A (H product, shifted steps),
  * 1 B (residual update; with S also the S product of the inner start),
  * 2 IC_A (S product of the inner CG), 3 IC_B (inner CG update), 4 C (rho);

@@ -304,13 +304,71 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     return warn;
 }
 
+// Panel width and CTAs per SM for a solve with panel_w == 0: for large solves,
+// time one iteration sequence of the solver's own kernels (profile path) for
+// each candidate and keep the lowest estimated time per column; results are
+// cached in the context per problem shape.  Small solves use the heuristic.
+int autotune(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, int32_t n_z, const int64_t *rhs_rows,
+             int64_t n_rhs, const int64_t *out_row_ptr, const int64_t *out_rows, const tb_solve_opts &opts,
+             int *W_out, int *cps_out) {
+    const bool mixed = opts.precision == TB_PREC_MIXED;
+    *W_out = panel_width_for((int)std::min<int64_t>(n_rhs, mixed ? 64 : 32));
+    *cps_out = opts.ctas_per_sm;
+    if (n_rhs < 128) return TB_OK; // tuning would cost more than it saves
+    tb_tune_key key{H->n_brows, H->nnzb, std::min<int64_t>(n_rhs, 64), H->bdim, S ? 1 : 0, opts.precision, n_z};
+    for (auto &kv : ctx->tuned)
+        if (kv.first == key) {
+            *W_out = kv.second.first;
+            *cps_out = kv.second.second;
+            return TB_OK;
+        }
+    double best = 1e300;
+    const int widths[4] = {8, 16, 32, 64};
+    const int cpss[2] = {2, 3};
+    for (int W : widths) {
+        if (W > n_rhs) break;
+        for (int cps : cpss) {
+            tb_solve_opts o = opts;
+            o.panel_w = W;
+            o.ctas_per_sm = cps;
+            o.stats = nullptr;
+            double ms[8] = {0};
+            int rc = run_solver(ctx, H, S, z, n_z, rhs_rows, W, out_row_ptr, out_rows, &o, nullptr, nullptr, nullptr,
+                                nullptr, 2, ms);
+            if (rc < 0) return rc;
+            const double inner = S ? 8.0 : 0.0;
+            const double per_col = (ms[0] + ms[1] + ms[4] + inner * (ms[2] + ms[3])) / W;
+            if (per_col < best) {
+                best = per_col;
+                *W_out = W;
+                *cps_out = cps;
+            }
+        }
+    }
+    ctx->tuned.push_back({key, {*W_out, *cps_out}});
+    return TB_OK;
+}
+
 } // namespace
 
 extern "C" int shifted_cocg_solve(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, int32_t n_z,
                                   const int64_t *rhs_rows, int64_t n_rhs, const int64_t *out_row_ptr,
                                   const int64_t *out_rows, const tb_solve_opts *opts, double *G, int32_t *iters,
                                   double *resid, int32_t *status) {
-    return run_solver(ctx, H, S, z, n_z, rhs_rows, n_rhs, out_row_ptr, out_rows, opts, G, iters, resid, status, 0,
+    if (!ctx) return TB_ERR_ARG;
+    tb_solve_opts o;
+    if (opts)
+        o = *opts;
+    else
+        tb_solve_opts_default(&o);
+    if (o.panel_w == 0 && n_rhs > 0 && H && z && rhs_rows && out_row_ptr) {
+        int W = 0, cps = 0;
+        int rc = autotune(ctx, H, S, z, n_z, rhs_rows, n_rhs, out_row_ptr, out_rows, o, &W, &cps);
+        if (rc < 0) return rc;
+        o.panel_w = W;
+        o.ctas_per_sm = cps;
+    }
+    return run_solver(ctx, H, S, z, n_z, rhs_rows, n_rhs, out_row_ptr, out_rows, &o, G, iters, resid, status, 0,
                       nullptr);
 }
 

@@ -57,9 +57,20 @@ __host__ __device__ __forceinline__ c64 to64(c32 a) { return mk((double)a.re, (d
 __host__ __device__ __forceinline__ c64 to64(c64 a) { return a; }
 
 // ------------------------------------------------------------------ status
+struct tb_tune_key {
+    int64_t n_brows, nnzb, n_rhs_cap;
+    int32_t bdim, has_s, precision, n_z;
+    bool operator==(const tb_tune_key &o) const {
+        return n_brows == o.n_brows && nnzb == o.nnzb && n_rhs_cap == o.n_rhs_cap && bdim == o.bdim &&
+               has_s == o.has_s && precision == o.precision && n_z == o.n_z;
+    }
+};
+
 struct tb_ctx {
     int device = 0;
     std::string last_error;
+    // autotuned (panel width, CTAs per SM) per problem shape
+    std::vector<std::pair<tb_tune_key, std::pair<int, int>>> tuned;
     // grow-only device workspace slots owned by the context
     std::vector<void *> ws_ptr;
     std::vector<size_t> ws_size;
