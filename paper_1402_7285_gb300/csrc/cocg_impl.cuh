@@ -743,7 +743,8 @@ struct SolveLaunch {
             k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
             k_rho<T, B, W><<<grid, block, 0, stream>>>(p, 1);
         }
-        cudaEvent_t ev[6];
+        // events: [0] A [1] B [2] (untimed first inner pair) [3] IC_A [4] IC_B [5] C [6]
+        cudaEvent_t ev[7];
         for (auto &e : ev) cudaEventCreate(&e);
         double acc[5] = {0, 0, 0, 0, 0};
         for (int r = 0; r < profile_reps && !rc; ++r) {
@@ -758,31 +759,32 @@ struct SolveLaunch {
             else
                 k_update_sI<T, B, W><<<grid, block, 0, stream>>>(p);
             cudaEventRecord(ev[2], stream);
-            int nev = 3;
+            int last = 2;
             if (has_s) {
                 // first inner iteration (no previous direction) untimed; time a
                 // steady-state one (k = 1), as most inner iterations of a solve are
                 k_inner_a<T, B, W><<<grid, block, 0, stream>>>(p);
                 k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
-                cudaEventRecord(ev[2], stream);
-                k_inner_a<T, B, W><<<grid, block, 0, stream>>>(p);
                 cudaEventRecord(ev[3], stream);
-                k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
+                k_inner_a<T, B, W><<<grid, block, 0, stream>>>(p);
                 cudaEventRecord(ev[4], stream);
-                k_rho<T, B, W><<<grid, block, 0, stream>>>(p, 0);
+                k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
                 cudaEventRecord(ev[5], stream);
-                nev = 6;
+                k_rho<T, B, W><<<grid, block, 0, stream>>>(p, 0);
+                cudaEventRecord(ev[6], stream);
+                last = 6;
             }
-            cudaError_t e = cudaEventSynchronize(ev[nev - 1]);
+            cudaError_t e = cudaEventSynchronize(ev[last]);
             if (e != cudaSuccess) {
                 rc = set_error(ctx, TB_ERR_CUDA, "profile: %s", cudaGetErrorString(e));
                 break;
             }
-            const int map[5] = {0, 1, 2, 3, 4};
-            for (int k = 0; k + 1 < nev; ++k) {
+            // (kernel, start event, end event)
+            const int spans[5][3] = {{0, 0, 1}, {1, 1, 2}, {2, 3, 4}, {3, 4, 5}, {4, 5, 6}};
+            for (int q = 0; q < (has_s ? 5 : 2); ++q) {
                 float ms = 0.f;
-                cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-                acc[map[k]] += ms;
+                cudaEventElapsedTime(&ms, ev[spans[q][1]], ev[spans[q][2]]);
+                acc[spans[q][0]] += ms;
             }
         }
         for (auto &e : ev) cudaEventDestroy(e);
