@@ -148,42 +148,73 @@ def kernel_traffic(kernel: str) -> int | None:
     return int(m.group(1)) if m else None
 
 
-def algorithmic_bytes(n_rows, nnzb, bdim, n_brows, W, n_z, n_ent, esz):
-    """Bytes each solver kernel must move once per launch (matrix read once, panel vectors once)."""
+def algorithmic_bytes(n_rows, nnzb, bdim, n_brows, W, n_z, n_ent, esz, dsz):
+    """Bytes each solver kernel must move once per launch (matrix read once, panel vectors once).
+
+    esz: bytes per real of the panel vectors; dsz: of the inner CG's direction
+    vectors (FP32 with df panels).  FP64 and df panels keep H p by recurrence
+    (read and written by A); FP32 panels do not."""
+    hp = 2 if esz == 8 else 0
     V = n_rows * W * 2 * esz                     # one complex panel vector
+    Vd = n_rows * W * 2 * dsz                    # one inner CG direction vector
     Mb = nnzb * bdim * bdim * esz + nnzb * 4 + (n_brows + 1) * 8
     proj = n_ent * n_z * 16                      # one FP64 complex projected-state array
     return {
-        "A_outer_H_product": 7 * V + Mb + 2 * proj,     # R, P_old, RT, SP in; P, SP, U out; p^m rw
+        "A_outer_H_product": (7 + hp) * V + Mb + 2 * proj,  # R, P_old, RT, SP, HP in; P, SP, U, HP out; p^m rw
         "B_update": 6 * V + Mb + 3 * proj,              # RT, U, R in; RT, R', T out; S; x^m rw, p^m in
-        "IC_A_inner_S_product": 4 * V + Mb,             # T, D_old in; D, A out; S
-        "IC_B_inner_update": 6 * V,                     # Y, D, T, A in; Y, T out
-        "C_rho": 2 * V,                                 # R, RT in
+        "IC_A_inner_S_product": 4 * V + 2 * Vd + Mb,    # T, D_old, Y in; D, A, Y out; S
+        "IC_B_inner_update": 3 * V,                     # T, A in; T out
+        "C_rho": 3 * V + Vd,                            # R, D, RT in; R out
     }
 
 
 # FP32 instructions per df operation as implemented (csrc/df64.cuh): a lazily
-# accumulated product term 12, a normalised df fma 15, a df multiply 7, a df add 11.
-DF_TERM, DF_FMA, DF_MUL, DF_ADD = 12, 15, 7, 11
+# accumulated product term 12 (11 with an FP32 operand), an identity-block
+# term 7, a normalised df fma 15 (14 with an FP32 operand), a df multiply 7
+# (6), a df add 11, a df value added to a two-float sum 8.
+DF_TERM, DF_TERM_F, DF_VAL, DF_FMA, DF_FMA_F, DF_MUL, DF_MUL_F, DF_ADD, ACC_ADD = 12, 11, 7, 15, 14, 7, 6, 11, 8
 FP32_PEAK_OPS = 152 * 128 * 2.07e9       # SMs x FP32 lanes x max SM clock (one op per lane per clock)
 
 
-def df_ops(n_rows, nnzb, bdim, W):
-    """FP32 instructions per launch of each solver kernel in df64 (complex panel of W)."""
+def df_ops(n_rows, nnzb, bdim, W, s_unit=True):
+    """FP32 instructions per launch of each df64 solver kernel.
+
+    'algorithmic' forms every vector element once; 'implemented' adds the
+    neighbour values that each product forms again on the fly (one per block
+    that references the row)."""
     bb = bdim * bdim
-    prod = nnzb * bb * W * 2 * DF_TERM                    # real block x complex panel, lazy sums
-    cx_axpy = 4 * DF_MUL + 4 * DF_ADD                     # x = a + s b, complex s (4 mul, 2+2 add)
-    re_axpy = 2 * DF_FMA                                  # x = a + s b, real s
-    nb_rows = nnzb * bdim * W                             # neighbour panel elements formed on the fly
-    own = n_rows * W
-    dot = 4 * DF_MUL + 4 * 8                              # complex product into two-float sums
-    return {
-        "A_outer_H_product": prod + nb_rows * cx_axpy + own * (2 * cx_axpy + 2 * DF_MUL + DF_ADD + dot),
-        "B_update": prod + nb_rows * cx_axpy + own * (2 * cx_axpy + 2 * DF_ADD + 2 * dot),
-        "IC_A_inner_S_product": prod + nb_rows * re_axpy + own * (re_axpy + dot),
-        "IC_B_inner_update": own * (4 * DF_FMA + dot),
-        "C_rho": own * dot,
+    n_br = n_rows // bdim
+    own = n_rows * W                                      # complex elements of one panel vector
+    nb = nnzb * bdim * W                                  # neighbour elements one product reads
+    prod_h = nnzb * bb * 2 * W * DF_TERM                  # real df block x complex df panel
+    if s_unit:                                            # identity diagonal blocks of S: additions only
+        prod_s = (nnzb - n_br) * bb * 2 * W * DF_TERM_F + n_br * bdim * 2 * W * DF_VAL
+    else:
+        prod_s = nnzb * bb * 2 * W * DF_TERM_F            # df block x FP32 panel (inner CG operands)
+    cx_axpy = 4 * DF_MUL + 4 * DF_ADD                     # a + s b, complex df s
+    dot = 4 * (DF_MUL + ACC_ADD)                          # complex bilinear product into two-float sums
+    norm = 2 * (DF_MUL + ACC_ADD)                         # Hermitian norm
+    alg = {
+        "A_outer_H_product": prod_h + own * (4 * cx_axpy + dot),     # p, Sp, Hp, u; mu
+        "B_update": prod_s + own * (4 + cx_axpy + 2 * DF_ADD + 2 * norm),
+        "IC_A_inner_S_product": prod_s + own * (2 + 2 * DF_FMA_F + 2 * (DF_MUL_F + ACC_ADD)),
+        "IC_B_inner_update": own * (2 * DF_FMA + norm),
+        "C_rho": own * (2 * DF_FMA_F + dot),
     }
+    extra = {"B_update": nb * 4, "IC_A_inner_S_product": nb * 2}
+    impl = {k: v + extra.get(k, 0) for k, v in alg.items()}
+    return alg, impl
+
+
+def unit_diagonal(S) -> bool:
+    """Every diagonal block of S (host Bsr) is the identity."""
+    if S is None:
+        return False
+    rp, ci = np.asarray(S.row_ptr), np.asarray(S.col_idx)
+    val = np.asarray(S.val).reshape(-1, S.bdim, S.bdim)
+    rows = np.repeat(np.arange(S.n_brows), np.diff(rp))
+    diag = val[ci == rows]
+    return diag.shape[0] == S.n_brows and bool(np.all(diag == np.eye(S.bdim)))
 
 
 def run_ours(args, rank, world):
@@ -324,20 +355,22 @@ def run_ours(args, rank, world):
     dom = max(share, key=share.get)
     n_ent = int(ptr[-1].item())
     esz = 4 if prec == tb.TB_PREC_MIXED else 8      # bytes per real: FP32, or FP64 / df pairs
-    algo = algorithmic_bytes(Hh.n_rows, Hh.nnzb, Hh.bdim, Hh.n_brows, W, n_z, n_ent, esz)
+    dsz = 4 if prec != tb.TB_PREC_FP64 else 8       # inner CG directions: FP32 with df panels
+    algo = algorithmic_bytes(Hh.n_rows, Hh.nnzb, Hh.bdim, Hh.n_brows, W, n_z, n_ent, esz, dsz)
     peaks = measured_peaks()
     achieved = algo[dom] / (prof[dom] * 1e-3) / 1e9
     hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
            "peak_source": peaks["source"] + " (burst, kernel timed alone)", "bytes_per_launch": algo[dom]}
     if prec == tb.TB_PREC_DF64:
         # double-float products are bound by the FP32 pipes (ncu: FMA pipe ~50-60% active), not by HBM
-        ops = df_ops(Hh.n_rows, Hh.nnzb, Hh.bdim, W)
+        ops, ops_impl = df_ops(Hh.n_rows, Hh.nnzb, Hh.bdim, W, s_unit=unit_diagonal(Sh))
         ach = ops[dom] / (prof[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_OPS / 1e12,
                 "unit": "TFLOP/s", "frac": ach / (FP32_PEAK_OPS / 1e12),
-                "op_definition": "FP32 operations of the df arithmetic as implemented, one per instruction; "
-                                 "peak = 152 SMs x 128 FP32 lanes x 2.07 GHz",
-                "ops_per_launch": ops[dom], "traffic": kernel_traffic(dom), "hbm": hbm}
+                "op_definition": "FP32 instructions of the df arithmetic with every vector element formed once "
+                                 "(one per lane per clock); peak = 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                "ops_per_launch": ops[dom], "ops_per_launch_implemented": ops_impl[dom],
+                "traffic": kernel_traffic(dom), "hbm": hbm}
     else:
         roof = {"bound": "alu" if prec == tb.TB_PREC_FP64 else "hbm", "kernel": dom, **hbm,
                 "traffic": kernel_traffic(dom)}
@@ -349,6 +382,115 @@ def run_ours(args, rank, world):
             "e2e": e2e, "roofline": roof, "outer_iters": outer, "inner_iters": inner, "fp64": fp64,
             "iters_per_column": [int(x) for r in results for x in (r.iters.cpu().numpy() if hasattr(r.iters, "cpu")
                                                                     else r.iters)]}
+
+
+LOCAL_WORKLOADS = {"c3": wl.C3, "c4": wl.C4, "c5": wl.C5}
+LOCAL_PRECISION = {"c3": "df64", "c4": "df64", "c5": "df64"}   # FP32 leaves ~12% of C3's pairs unconverged
+
+
+def run_local(args):
+    """Localized right-hand sides on hop-shell subspaces (C3-C5), persistent solver.
+
+    One step solves --local-cols columns (one launch of the persistent kernel,
+    each CTA taking the next column as soon as its own converges) and reduces
+    the kept entries to LDOS; c4 also trains the iteration-count predictor on
+    --train-cols other columns (untimed) and orders the queue with it."""
+    import time as _time
+
+    import torch
+
+    import paper_1402_7285_gb300 as tb
+    from paper_1402_7285_gb300 import scheduler
+
+    w = LOCAL_WORKLOADS[args.workload]
+    prec_name = args.precision if args.precision_given else LOCAL_PRECISION[args.workload]
+    prec = {"mixed": tb.TB_PREC_MIXED, "fp64": tb.TB_PREC_FP64, "df64": tb.TB_PREC_DF64}[prec_name]
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    t0 = _time.perf_counter()
+    Hh, Sh, _ = tb.build_system(w.system, w.seed)
+    H = Hh.to(dev)
+    S = Sh.to(dev) if Sh is not None else None
+    build_s = _time.perf_counter() - t0
+    rows, rad = wl.rhs_of(w, n_atoms=Hh.n_brows)
+    perm = np.random.default_rng(w.seed).permutation(len(rows))
+    rows, rad = rows[perm], rad[perm]
+    n_step = args.local_cols
+    n_tr = args.train_cols if args.workload == "c4" else 0
+    need = n_tr + n_step * (args.warmup + args.steps + 1)
+    rows, rad = rows[:need], rad[:need]
+    sptr, satoms = tb.local_subspaces(Hh, rows, rad)
+    z = wl.shifts_of(w)
+    ctx = tb.Context()
+
+    def subset(lo, hi):
+        sp = (sptr[lo:hi + 1] - sptr[lo]).astype(np.int64)
+        sa = satoms[sptr[lo]:sptr[hi]]
+        r = rows[lo:hi]
+        return r, rad[lo:hi], sp, sa, np.arange(hi - lo + 1, dtype=np.int64), r.copy()
+
+    def solve(lo, hi, order=None):
+        r, rd, sp, sa, optr, orows = subset(lo, hi)
+        res = tb.solve_local(ctx, H, S, z, r, sp, sa, optr, orows, order=order, tol=w.tol, precision=prec,
+                             max_iter=args.max_iter)
+        return res
+
+    learned = None
+    if n_tr:
+        r, rd, sp, sa, optr, orows = subset(0, n_tr)
+        Dtr = tb.descriptors(ctx, H, S, r, rd, sp, sa).cpu().numpy()
+        res = solve(0, n_tr)
+        its = res.iters.cpu().numpy().astype(np.float64)
+        learned, hist = scheduler.train(ctx, Dtr, its, epochs=60, batch=256, lr=2e-3)
+
+    def order_for(lo, hi):
+        if learned is None:
+            return None
+        r, rd, sp, sa, optr, orows = subset(lo, hi)
+        D = tb.descriptors(ctx, H, S, r, rd, sp, sa).cpu().numpy()
+        return scheduler.longest_first(scheduler.predict(ctx, learned, D) * np.diff(sp) * Hh.bdim)
+
+    base = n_tr
+    for s_ in range(args.warmup):
+        lo = base + s_ * n_step
+        solve(lo, lo + n_step, order_for(lo, lo + n_step))
+    torch.cuda.synchronize()
+    pairs = total_pairs = 0
+    t_learn = 0.0
+    for s_ in range(args.steps):
+        lo = base + (args.warmup + s_) * n_step
+        torch.cuda.synchronize()
+        t1 = _time.perf_counter()
+        order = order_for(lo, lo + n_step)           # descriptors + prediction are part of the step
+        res = solve(lo, lo + n_step, order)
+        torch.cuda.synchronize()
+        t_learn += _time.perf_counter() - t1
+        ok = res.resid.cpu().numpy() <= w.tol
+        pairs += int(ok.sum())
+        total_pairs += ok.size
+    value = pairs / t_learn
+    sched = None
+    if learned is not None:
+        lo = base + args.warmup * n_step
+        torch.cuda.synchronize()
+        t1 = _time.perf_counter()
+        solve(lo, lo + n_step, None)
+        torch.cuda.synchronize()
+        t_plain = _time.perf_counter() - t1
+        t_first = t_learn / args.steps
+        sched = {"plain_order_s": t_plain, "learned_order_s_mean": t_first, "train_cols": n_tr}
+    ctx.close()
+    s = w.system
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_learn * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec_name, "data": "synthetic",
+            "config": {"workload": f"{w.name}: {s.lattice}, {Hh.n_brows} atoms x {s.bdim} orbitals, "
+                                   f"{w.n_shifts} shifts E+{w.eta}i, local subspaces radius {w.radii}",
+                       "columns_per_step": n_step, "tol": w.tol, "precision": prec_name,
+                       "solver": "persistent one-CTA-per-column local subspace solver"},
+            "build_s": build_s, "scheduler": sched, "converged_frac": pairs / max(total_pairs, 1),
+            "mean_subspace_atoms": float(np.mean(np.diff(sptr)))}
+    print(json.dumps(line))
 
 
 def cpu_oracle_sample(target_seconds: float, iters_needed: float | None):
@@ -396,6 +538,10 @@ def main():
                     help="only launch the solver kernels of one panel (CUDA events; for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=100000)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2: the metric's configuration (panel solver); c3-c5: localized columns")
+    ap.add_argument("--local-cols", type=int, default=2048)
+    ap.add_argument("--train-cols", type=int, default=4096)
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
                     help="skip timing one panel with the plain FP64 solver")
     ap.add_argument("--no-e2e", action="store_true")
@@ -404,7 +550,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
+    args.precision_given = any(a.startswith("--precision") for a in sys.argv[1:])
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload != "c2" and args.impl == "ours":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_local(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
 
     if args.impl == "reference":

@@ -141,7 +141,10 @@ int tb_build_csr(const tb_system_spec *spec, uint64_t seed, tb_bsr *H, tb_bsr *S
                            tests, projected solutions and reductions           */
 #define TB_PREC_DF64 2  /* vectors, SpMM and updates in double-float (hi + lo
                            FP32 pairs, ~48 bits) on the FP32 pipes; FP64
-                           scalars, projections and reductions as above        */
+                           scalars, projections and reductions as above; the
+                           inner CG's search directions and starting guess
+                           (which steer it but do not enter its result) in
+                           FP32                                                */
 
 /* Y = A X for a real BSR matrix A (n = n_brows*bdim rows) and a complex panel
  * X of ncols columns: X, Y complex double [n][ncols] (row-major, interleaved).
@@ -191,7 +194,10 @@ void tb_solve_opts_default(tb_solve_opts *opts);
  * Method: one seed COCG per column in the S-bilinear form with the shifted
  * systems following through collinear residuals (Sec. 3; recurrences in the
  * library's design notes), columns batched into panels so that one block
- * sparse product per iteration serves every column and every shift.
+ * sparse product per iteration serves every column and every shift.  When
+ * every diagonal block of S is the identity (orthonormal orbitals on each
+ * site; checked on the device per call) the S products add those blocks'
+ * operand instead of multiplying by them, with the same result bits.
  * Returns TB_OK, or a positive OR of TB_WARN_* when some column did not
  * converge, or a negative error. */
 int shifted_cocg_solve(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z,
@@ -234,9 +240,12 @@ int tb_local_subspaces(const tb_bsr *A, const int64_t *rhs_rows, const int32_t *
  * outside O_c give 0).  S (NULL = I) must have H's block pattern.  `order`
  * (optional, a permutation of 0..n_rhs-1) is the order in which columns are
  * taken from the device work queue: each CTA solves one column at a time in
- * shared memory and takes the next as soon as it finishes.  opts->panel_w is
- * ignored; n_z <= 1024.  Outputs and status as shifted_cocg_solve.
- * TB_ERR_SIZE when the largest subspace does not fit one CTA's shared memory. */
+ * shared memory and takes the next as soon as it finishes.  When the vectors
+ * of the largest subspace do not fit one CTA's shared memory they are placed
+ * in a device workspace of (grid x vectors) instead (read through L2).
+ * opts->panel_w is ignored; n_z <= 1024.  Outputs and status as
+ * shifted_cocg_solve.  TB_ERR_SIZE when even the per-shift states and the
+ * local block structure do not fit shared memory. */
 int shifted_cocg_solve_local(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, int32_t n_z,
                              const int64_t *rhs_rows, int64_t n_rhs, const int64_t *sub_ptr,
                              const int32_t *sub_atoms, const int64_t *out_row_ptr, const int64_t *out_rows,

@@ -7,6 +7,23 @@ __global__ void k_copy_z(const double *z, c64 *zc, int nz) {
     for (int i = threadIdx.x; i < nz; i += blockDim.x) zc[i] = mk(z[2 * i], z[2 * i + 1]);
 }
 
+// *not_unit = 1 unless every block row holds a diagonal block equal to the
+// identity (the overlap of orthonormal orbitals on one site).
+__global__ void k_unit_diag(const int64_t *rp, const int32_t *ci, const double *val, int64_t n_brows, int b,
+                            int *not_unit) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t br = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; br < n_brows; br += stride) {
+        bool ok = false;
+        for (int64_t k = rp[br]; k < rp[br + 1]; ++k) {
+            if (ci[k] != br) continue;
+            ok = true;
+            for (int q = 0; q < b * b; ++q)
+                if (val[k * b * b + q] != ((q / b == q % b) ? 1.0 : 0.0)) ok = false;
+        }
+        if (!ok) atomicOr(not_unit, 1);
+    }
+}
+
 } // namespace tbgf
 
 // =================================================================== entry points
@@ -155,11 +172,24 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     if (!rc && has_s)
         rc = validate_bsr(ctx, (const int64_t *)d_srp, (const int32_t *)d_sci, d_sval, S->n_brows, S->nnzb, stream, "S");
     if (rc) return rc;
+    int s_unit = 0;
+    if (has_s) {
+        int *flag = nullptr;
+        TB_CUDA_TRY(ctx, cudaMallocAsync((void **)&flag, sizeof(int), stream));
+        TB_CUDA_TRY(ctx, cudaMemsetAsync(flag, 0, sizeof(int), stream));
+        k_unit_diag<<<num_sms() * 4, 256, 0, stream>>>((const int64_t *)d_srp, (const int32_t *)d_sci,
+                                                      (const double *)d_sval, S->n_brows, b, flag);
+        int h = 1;
+        TB_CUDA_TRY(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        TB_CUDA_TRY(ctx, cudaFreeAsync(flag, stream));
+        TB_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        s_unit = h == 0;
+    }
 
     // ---- workspace
     const size_t esz = mixed ? 4 : 8;
     const size_t vec_bytes = align_up(esz * 2 * n_rows * W, 256);
-    const int n_vec = has_s ? 11 : 4;
+    const int n_vec = (has_s ? 11 : 4) + (mixed ? 0 : 1); // + H p (recurrence) unless FP32
     const int per_cta = NT / (W / (mixed ? 2 : 1));
     TB_CHECK(ctx, opts.ctas_per_sm >= 0 && opts.ctas_per_sm <= 8, TB_ERR_ARG, "ctas_per_sm must be 0..8");
     const int per_sm = opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 3;
@@ -228,6 +258,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.s_rp = (const int64_t *)d_srp;
     p.s_ci = (const int32_t *)d_sci;
     p.s_val = (const double *)sval;
+    p.s_unit = s_unit;
     p.n_brows = H->n_brows;
     char *vb = (char *)vec_base;
     int vi = 0;
@@ -236,6 +267,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.P[0] = vec();
     p.P[1] = vec();
     p.U = vec();
+    p.HP = mixed ? nullptr : vec();
     if (has_s) {
         p.R[0] = vec();
         p.R[1] = vec();

@@ -84,6 +84,7 @@ __global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
             p.D[1][o] = p.D[1][o + 1] = 0;
             p.Av[o] = p.Av[o + 1] = 0;
         }
+        if (p.HP) p.HP[o] = p.HP[o + 1] = 0;
     }
     const int64_t ne = (int64_t)p.max_ent * p.nz;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ne; t += stride) {
@@ -213,10 +214,15 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
+    // H p_n: with FP64 and df panels, H r_n + beta_{n-1} (H p_{n-1}) (one
+    // product of the finished r_n, H p kept by this recurrence, so the product
+    // reads plain neighbour rows); with FP32 panels, the product of p_n formed
+    // on the fly from r_n and p_{n-1}.
+    constexpr bool HP_REC = !std::is_same<T, float>::value;
     const int n = p.ctl->n;
     const T *Rc = HAS_S ? p.R[n & 1] : p.RT;
     T *Pnew = p.P[n & 1];
-    LdAxpy<T, W> ld;
+    LdAxpy<T, W> ld; // p_n = r_n + beta_{n-1} p_{n-1}
     ld.a = Rc;
     ld.b = p.P[(n + 1) & 1];
     ld.lane = lane;
@@ -225,6 +231,8 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
         const ColState &C = p.col[lane * CPT + cc];
         ld.s[cc] = C.done ? mk<T>(0, 0) : cvt<T>(C.beta_prev);
     }
+    LdAxpy<T, W> lr = ld; // r_n
+    lr.b = nullptr;
     const cpx<T> zs = cvt<T>(p.zs);
     Acc<T> acc[CPT][2];
 #pragma unroll
@@ -233,13 +241,23 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
     cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
     for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
         cpx<T> y[B][CPT];
-        bsr_row_product<T, B>(p.h_rp, p.h_ci, p.h_val, br, ld, y);
+        if constexpr (HP_REC)
+            bsr_row_product<T, B>(p.h_rp, p.h_ci, p.h_val, br, lr, y);
+        else
+            bsr_row_product<T, B>(p.h_rp, p.h_ci, p.h_val, br, ld, y);
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int64_t row = br * B + i;
             cpx<T> pv[CPT], u[CPT];
             ld(row, pv);
             st_row<T, W>(Pnew, row, lane, pv);
+            if constexpr (HP_REC) {
+                cpx<T> hp[CPT];
+                ld_row<T, W>(p.HP, row, lane, hp);
+#pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) y[i][cc] = y[i][cc] + ld.s[cc] * hp[cc];
+                st_row<T, W>(p.HP, row, lane, y[i]);
+            }
             if constexpr (HAS_S) {
                 cpx<T> rt[CPT], sp[CPT];
                 ld_row<T, W>(p.RT, row, lane, rt);
@@ -389,18 +407,20 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
+    typedef typename DirOf<T>::type X;
     const int n = p.ctl->n;
     const T *Rc = p.R[n & 1];
     T *Rn = p.R[(n + 1) & 1];
-    LdAxpy<T, W> ld; // y_0 = r_n - alpha_n u
-    ld.a = Rc;
-    ld.b = p.U;
+    LdGuess<T, W> ld; // y_0 = r_n - alpha_n u
+    ld.r = Rc;
+    ld.u = p.U;
     ld.lane = lane;
     cpx<T> a[CPT];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
-        a[cc] = cvt<T>(p.col[lane * CPT + cc].alpha);
-        ld.s[cc] = mk<T>(-a[cc].re, -a[cc].im);
+        const c64 al = p.col[lane * CPT + cc].alpha;
+        a[cc] = cvt<T>(al);
+        ld.s[cc] = mk((X)(-al.re), (X)(-al.im));
     }
     Acc<T> acc[CPT][2];
 #pragma unroll
@@ -409,16 +429,18 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
     cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
     for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
         cpx<T> sy[B][CPT];
-        bsr_row_product<T, B>(p.s_rp, p.s_ci, p.s_val, br, ld, sy);
+        bsr_row_product<T, B, X>(p.s_rp, p.s_ci, p.s_val, br, ld, sy, p.s_unit ? br : -1);
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int64_t row = br * B + i;
             cpx<T> rt[CPT], u[CPT], y0[CPT], t[CPT];
+            cpx<X> g[CPT];
             ld_row<T, W>(p.RT, row, lane, rt);
             ld_row<T, W>(p.U, row, lane, u);
-            ld(row, y0);
+            ld(row, g);
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
+                y0[cc] = mk((T)g[cc].re, (T)g[cc].im);
                 rt[cc] = rt[cc] - a[cc] * u[cc];
                 t[cc] = rt[cc] - sy[i][cc];
                 acc[cc][0].add(rt[cc].re * rt[cc].re);
@@ -468,14 +490,22 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_a(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
+    typedef typename DirOf<T>::type X;
     const int k = p.ctl->k;
-    T *Dn = p.D[k & 1];
-    LdAxpyReal<T, W> ld; // d_k = t_k + beta d_{k-1}, beta real
-    ld.a = p.Tv;
-    ld.b = (k == 0) ? nullptr : p.D[(k + 1) & 1];
+    X *Dn = p.D[k & 1];
+    LdDir<T, W> ld; // d_k = t_k + beta d_{k-1}, beta real
+    ld.t = p.Tv;
+    ld.d = (k == 0) ? nullptr : p.D[(k + 1) & 1];
     ld.lane = lane;
+    // the previous iteration's solution update y += alpha_{k-1} d_{k-1}, due
+    // here (the step length is known and d_{k-1} is read anyway)
+    T *Y = p.R[(p.ctl->n + 1) & 1];
+    T ya[CPT];
 #pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) ld.s[cc] = (T)p.col[lane * CPT + cc].in_beta;
+    for (int cc = 0; cc < CPT; ++cc) {
+        ld.s[cc] = (X)p.col[lane * CPT + cc].in_beta;
+        ya[cc] = (T)p.col[lane * CPT + cc].in_alpha;
+    }
     Acc<T> acc[CPT][1];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero();
@@ -483,18 +513,30 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_a(Panel<T> p) {
     cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
     for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
         cpx<T> sd[B][CPT];
-        bsr_row_product<T, B>(p.s_rp, p.s_ci, p.s_val, br, ld, sd);
+        bsr_row_product<T, B, X>(p.s_rp, p.s_ci, p.s_val, br, ld, sd, p.s_unit ? br : -1);
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int64_t row = br * B + i;
-            cpx<T> d[CPT];
+            cpx<X> d[CPT];
             ld(row, d);
-            st_row<T, W>(Dn, row, lane, d);
+            st_dir<T, W>(Dn, row, lane, d);
             st_row<T, W>(p.Av, row, lane, sd[i]);
+            if (ld.d) {
+                cpx<T> y[CPT];
+                cpx<X> dp[CPT];
+                ld_row<T, W>(Y, row, lane, y);
+                ld_dir<T, W>(ld.d, row, lane, dp);
+#pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) {
+                    y[cc].re = fma_x(ya[cc], dp[cc].re, y[cc].re);
+                    y[cc].im = fma_x(ya[cc], dp[cc].im, y[cc].im);
+                }
+                st_row<T, W>(Y, row, lane, y);
+            }
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
-                acc[cc][0].add(d[cc].re * sd[i][cc].re);
-                acc[cc][0].add(d[cc].im * sd[i][cc].im);
+                acc[cc][0].add(mul_x(sd[i][cc].re, d[cc].re));
+                acc[cc][0].add(mul_x(sd[i][cc].im, d[cc].im));
             }
         }
     }
@@ -524,10 +566,6 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
-    const int k = p.ctl->k;
-    const int n = p.ctl->n;
-    const T *D = p.D[k & 1];
-    T *Y = p.R[(n + 1) & 1];
     T a[CPT]; // inner CG step length (real)
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) a[cc] = (T)p.col[lane * CPT + cc].in_alpha;
@@ -540,19 +578,15 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int64_t row = br * B + i;
-            cpx<T> y[CPT], d[CPT], t[CPT], av[CPT];
-            ld_row<T, W>(Y, row, lane, y);
-            ld_row<T, W>(D, row, lane, d);
+            cpx<T> t[CPT], av[CPT];
             ld_row<T, W>(p.Tv, row, lane, t);
             ld_row<T, W>(p.Av, row, lane, av);
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
-                y[cc] = y[cc] + a[cc] * d[cc];
                 t[cc] = t[cc] - a[cc] * av[cc];
                 acc[cc][0].add(t[cc].re * t[cc].re);
                 acc[cc][0].add(t[cc].im * t[cc].im);
             }
-            st_row<T, W>(Y, row, lane, y);
             st_row<T, W>(p.Tv, row, lane, t);
         }
     }
@@ -590,8 +624,15 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_rho(Panel<T> p, int in
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
+    typedef typename DirOf<T>::type X;
     const int n = p.ctl->n;
-    const T *Rn = p.R[(n + 1) & 1];
+    T *Rn = p.R[(n + 1) & 1];
+    // the inner CG's last solution update, r_{n+1} += alpha d (alpha = 0 for
+    // columns whose update was already applied, and when no inner step ran)
+    const X *Dl = p.D[(p.ctl->k + 1) & 1];
+    T ya[CPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) ya[cc] = (T)p.col[lane * CPT + cc].in_alpha;
     Acc<T> acc[CPT][2];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero();
@@ -602,7 +643,15 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_rho(Panel<T> p, int in
         for (int i = 0; i < B; ++i) {
             const int64_t row = br * B + i;
             cpx<T> r[CPT], rt[CPT];
+            cpx<X> dl[CPT];
             ld_row<T, W>(Rn, row, lane, r);
+            ld_dir<T, W>(Dl, row, lane, dl);
+#pragma unroll
+            for (int cc = 0; cc < CPT; ++cc) {
+                r[cc].re = fma_x(ya[cc], dl[cc].re, r[cc].re);
+                r[cc].im = fma_x(ya[cc], dl[cc].im, r[cc].im);
+            }
+            st_row<T, W>(Rn, row, lane, r);
             ld_row<T, W>(p.RT, row, lane, rt);
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {

@@ -6,7 +6,8 @@
 // iteration n (restated from the shifted-Krylov mathematics; rt = S r is the
 // residual of the original equation):
 //   A : p_n = r_n + beta_{n-1} p_{n-1};  Sp_n = rt_n + beta_{n-1} Sp_{n-1};
-//       u = z_s Sp_n - H p_n;  mu_n = p_n^T u;        (one BSR product with H)
+//       Hp_n = H r_n + beta_{n-1} Hp_{n-1} (FP32 panels: H p_n);
+//       u = z_s Sp_n - Hp_n;  mu_n = p_n^T u;         (one BSR product with H)
 //       per (slot, shift): pi rotation, residual test, p^m_n on the kept rows;
 //       last CTA: alpha_n = rho_n / mu_n, column done/breakdown, panel done.
 //   B : (S = I) rt_{n+1} = rt_n - alpha_n u; rho_{n+1} = rt^T rt; ||rt||^2;
@@ -14,9 +15,11 @@
 //       last CTA: beta_n, iteration count, loop condition.
 //   B': (S != I) rt_{n+1} = rt_n - alpha_n u; y_0 = r_n - alpha_n u;
 //       t_0 = rt_{n+1} - S y_0 (one BSR product with S); shifted updates as B;
-//       then the inner CG on S: IC_A (d = t + b d, a = S d, d^H a) and
-//       IC_B (y += a d, t -= a a, t^H t), repeated in a device-side loop;
-//   C : rho_{n+1} = r_{n+1}^T rt_{n+1}; last CTA as in B.
+//       then the inner CG on S: IC_A (y += a_prev d_prev, d = t + b d,
+//       a = S d, d^H a) and IC_B (t -= a a, t^H t), repeated in a device-side
+//       loop (each solution update is applied one step late, by the next IC_A
+//       or by C, which reads d_prev anyway);
+//   C : r_{n+1} = y += a_last d_last; rho_{n+1} = r_{n+1}^T rt_{n+1}; last CTA as in B.
 // All recurrence scalars are FP64.  The loop runs as CUDA-graph conditional
 // WHILE nodes whose conditions the last CTA of B / C / IC_B sets; every loop
 // has a hard iteration cap, so the device loop always ends.
@@ -61,6 +64,21 @@ struct Ctrl {
     int64_t pad[4];
 };
 
+// Vectors of the inner CG on S that only steer it: its search direction d and
+// its starting guess y_0.  With df panels they are FP32 (a perturbation of a
+// direction or of a starting guess changes which iterate the inner CG visits,
+// not what it converges to: the products S d, the residual t and the solution
+// y stay df, and y and t are updated with the same d, so t = rt - S y holds
+// to df rounding whatever d is).  FP64 and FP32 panels keep their own type.
+template <typename T>
+struct DirOf {
+    typedef T type;
+};
+template <>
+struct DirOf<df> {
+    typedef float type;
+};
+
 template <typename T>
 struct Panel {
     // matrices (values in T)
@@ -70,9 +88,12 @@ struct Panel {
     const int64_t *s_rp;
     const int32_t *s_ci;
     const T *s_val;
+    int32_t s_unit;   // every diagonal block of S is the identity
     int64_t n_brows;
     // panel vectors [n_rows][W] complex T
-    T *R[2], *RT, *P[2], *SP, *U, *Tv, *D[2], *Av;
+    T *R[2], *RT, *P[2], *SP, *U, *Tv, *Av;
+    T *HP;                         // H p_n by recurrence (FP64 and df panels; null for FP32)
+    typename DirOf<T>::type *D[2]; // inner CG directions (FP32 for df panels)
     // state
     ColState *col;   // [W]
     ShiftState *sh;  // [W][nz]
@@ -273,30 +294,99 @@ struct LdAxpy {
     }
 };
 
-// x = a(row) + s .* b(row) with real per-column scalars s
-template <typename T, int W>
-struct LdAxpyReal {
-    const T *a;
-    const T *b;
-    T s[PanelVec<T>::CPT];
-    int lane;
-    __device__ __forceinline__ void operator()(int64_t row, cpx<T> (&x)[PanelVec<T>::CPT]) const {
-        ld_row<T, W>(a, row, lane, x);
-        if (b) {
-            cpx<T> y[PanelVec<T>::CPT];
-            ld_row<T, W>(b, row, lane, y);
-#pragma unroll
-            for (int c = 0; c < PanelVec<T>::CPT; ++c) {
-                x[c].re = fma(s[c], y[c].re, x[c].re);
-                x[c].im = fma(s[c], y[c].im, x[c].im);
-            }
-        }
-    }
-};
 
 template <typename T>
 __device__ __forceinline__ cpx<T> cvt(c64 v) {
     return mk((T)v.re, (T)v.im);
 }
+
+// Load / store CPT complex values of a direction panel row (layout of the
+// panel type T, element type DirOf<T>: a df panel's directions are one
+// float2 per lane).
+template <typename T, int W>
+__device__ __forceinline__ void ld_dir(const typename DirOf<T>::type *__restrict__ base, int64_t row, int lane,
+                                       cpx<typename DirOf<T>::type> (&x)[PanelVec<T>::CPT]) {
+    if constexpr (std::is_same<T, df>::value) {
+        const float2 v = *reinterpret_cast<const float2 *>(base + (row * W + lane) * 2);
+        x[0] = mk(v.x, v.y);
+    } else {
+        ld_row<T, W>(base, row, lane, x);
+    }
+}
+template <typename T, int W>
+__device__ __forceinline__ void st_dir(typename DirOf<T>::type *__restrict__ base, int64_t row, int lane,
+                                       const cpx<typename DirOf<T>::type> (&x)[PanelVec<T>::CPT]) {
+    if constexpr (std::is_same<T, df>::value) {
+        *reinterpret_cast<float2 *>(base + (row * W + lane) * 2) = make_float2(x[0].re, x[0].im);
+    } else {
+        st_row<T, W>(base, row, lane, x);
+    }
+}
+
+// a * b and c + a * b with b of the direction type
+__device__ __forceinline__ df mul_x(df a, float b) { return mul_f(a, b); }
+__device__ __forceinline__ float mul_x(float a, float b) { return a * b; }
+__device__ __forceinline__ double mul_x(double a, double b) { return a * b; }
+__device__ __forceinline__ df fma_x(df a, float b, df c) { return fma_f(a, b, c); }
+__device__ __forceinline__ float fma_x(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_x(double a, double b, double c) { return ::fma(a, b, c); }
+
+// Inner CG direction d_k = t_k + beta d_{k-1} (real beta per column; d_{k-1}
+// absent at k = 0), formed in the direction type.
+template <typename T, int W>
+struct LdDir {
+    typedef typename DirOf<T>::type X;
+    const T *t;
+    const X *d;
+    X s[PanelVec<T>::CPT];
+    int lane;
+    __device__ __forceinline__ void operator()(int64_t row, cpx<X> (&x)[PanelVec<T>::CPT]) const {
+        constexpr int CPT = PanelVec<T>::CPT;
+        if constexpr (std::is_same<T, df>::value) {
+            cpx<df> tv[1];
+            ld_row<df, W>(t, row, lane, tv);
+            x[0] = mk(tv[0].re.hi, tv[0].im.hi);
+        } else {
+            ld_row<T, W>(t, row, lane, x);
+        }
+        if (d) {
+            cpx<X> y[CPT];
+            ld_dir<T, W>(d, row, lane, y);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                x[c].re = fma_x(s[c], y[c].re, x[c].re);
+                x[c].im = fma_x(s[c], y[c].im, x[c].im);
+            }
+        }
+    }
+};
+
+// Starting guess of the inner CG, y_0 = r_n - alpha_n u (complex alpha per
+// column), formed in the direction type.
+template <typename T, int W>
+struct LdGuess {
+    typedef typename DirOf<T>::type X;
+    const T *r;
+    const T *u;
+    cpx<X> s[PanelVec<T>::CPT]; // -alpha_n
+    int lane;
+    __device__ __forceinline__ void operator()(int64_t row, cpx<X> (&x)[PanelVec<T>::CPT]) const {
+        constexpr int CPT = PanelVec<T>::CPT;
+        if constexpr (std::is_same<T, df>::value) {
+            cpx<df> rv[1], uv[1];
+            ld_row<df, W>(r, row, lane, rv);
+            ld_row<df, W>(u, row, lane, uv);
+            const float ur = uv[0].re.hi, ui = uv[0].im.hi;
+            x[0].re = fmaf(s[0].re, ur, fmaf(-s[0].im, ui, rv[0].re.hi));
+            x[0].im = fmaf(s[0].re, ui, fmaf(s[0].im, ur, rv[0].im.hi));
+        } else {
+            cpx<T> uv[CPT];
+            ld_row<T, W>(r, row, lane, x);
+            ld_row<T, W>(u, row, lane, uv);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) x[c] = x[c] + s[c] * uv[c];
+        }
+    }
+};
 
 } // namespace tbgf

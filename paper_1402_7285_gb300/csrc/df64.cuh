@@ -92,8 +92,45 @@ struct DfSum {
         s = t.hi;
         c = DF_ADD(c, DF_ADD(t.lo, e));
     }
+    // b exact in FP32 (no low part): 11 operations
+    __device__ __forceinline__ void add_prod(df a, float b) {
+        const float p = DF_MUL(a.hi, b);
+        float e = fmaf(a.hi, b, -p);
+        e = fmaf(a.lo, b, e);
+        const df t = df_two_sum(s, p);
+        s = t.hi;
+        c = DF_ADD(c, DF_ADD(t.lo, e));
+    }
+    // a plain value (a product with 1): the same operations on s and c as
+    // add_prod(1, x), without the multiplications
+    __device__ __forceinline__ void add_val(df x) {
+        const df t = df_two_sum(s, x.hi);
+        s = t.hi;
+        c = DF_ADD(c, DF_ADD(t.lo, x.lo));
+    }
+    __device__ __forceinline__ void add_val(float x) {
+        const df t = df_two_sum(s, x);
+        s = t.hi;
+        c = DF_ADD(c, t.lo);
+    }
     __device__ __forceinline__ df value() const { return df_fast_two_sum(s, c); }
 };
+
+// a * b and c + a * b for an FP32 operand b (its low part is zero); named, not
+// overloaded, so that a double operand never binds to them by narrowing
+__host__ __device__ __forceinline__ df mul_f(df a, float b) {
+    const float p = DF_MUL(a.hi, b);
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return df_fast_two_sum(p, e);
+}
+__host__ __device__ __forceinline__ df fma_f(df a, float b, df c) {
+    const float p = DF_MUL(a.hi, b);
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    const df s = df_two_sum(c.hi, p);
+    return df_fast_two_sum(s.hi, DF_ADD(s.lo, DF_ADD(e, c.lo)));
+}
 
 __device__ __forceinline__ df ldg_val(const df *p) {
     const float2 v = __ldg(reinterpret_cast<const float2 *>(p));

@@ -148,6 +148,12 @@ extern "C" int shifted_cocg_solve_local(tb_ctx *ctx, const tb_bsr *H, const tb_b
         return o;
     };
     const size_t o_scr = take(sizeof(c64) * 2 * (size_t)max_kept * n_z * grid);
+    // subspace vectors in global memory when they do not fit in shared memory
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t csz = mixed ? 8 : 16;
+    const bool vec_global = local_smem(maxa, dmax, max_kept, n_z, has_s, b, csz, true) > (size_t)optin;
+    const size_t o_gvec = vec_global ? take(local_vec_bytes(maxa, b, csz, has_s) * grid) : 0;
     const size_t o_zc = take(sizeof(c64) * n_z);
     const size_t o_q = take(sizeof(unsigned long long) * 4);
     const size_t vsz = mixed ? sizeof(float) : sizeof(double);
@@ -204,6 +210,7 @@ extern "C" int shifted_cocg_solve_local(tb_ctx *ctx, const tb_bsr *H, const tb_b
     la.dmax = dmax;
     la.max_kept = max_kept;
     la.scratch = (c64 *)(ws + o_scr);
+    la.gvec = vec_global ? (void *)(ws + o_gvec) : nullptr;
     la.queue = (unsigned long long *)(ws + o_q);
     la.stat = (unsigned long long *)(ws + o_q) + 1;
     la.tol = opts.tol;

@@ -44,6 +44,7 @@ struct LocalArgs {
     int64_t n;
     int32_t maxa, dmax, max_kept;
     c64 *scratch; // [gridDim.x][2][max_kept][nz]
+    void *gvec;   // null: vectors in shared memory; else [gridDim.x][NV][maxa*B] cpx<T> in global memory
     unsigned long long *queue;
     unsigned long long *stat; // [2]: outer, inner iterations
     double tol, inner_tol;
@@ -120,13 +121,16 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NV = HAS_S ? 8 : 3;
     const int maxr = a.maxa * B;
-    cpx<T> *vec = reinterpret_cast<cpx<T> *>(smem);
+    // the subspace vectors live in shared memory, or (subspaces too large for
+    // it) in this CTA's slice of a global array, which stays in L2
+    cpx<T> *vec = a.gvec ? reinterpret_cast<cpx<T> *>(a.gvec) + (int64_t)blockIdx.x * NV * maxr
+                         : reinterpret_cast<cpx<T> *>(smem);
     cpx<T> *RT = vec;               // rt (= r when S = I)
     cpx<T> *P = vec + maxr;
     cpx<T> *U = vec + 2 * maxr;
     cpx<T> *R = HAS_S ? vec + 3 * maxr : RT;
     cpx<T> *SP = vec + 4 * maxr, *Tv = vec + 5 * maxr, *D = vec + 6 * maxr, *Av = vec + 7 * maxr;
-    ShiftL *shs = reinterpret_cast<ShiftL *>(vec + NV * maxr);
+    ShiftL *shs = a.gvec ? reinterpret_cast<ShiftL *>(smem) : reinterpret_cast<ShiftL *>(vec + NV * maxr);
     int32_t *atoms = reinterpret_cast<int32_t *>(shs + a.nz);
     int32_t *nbk = atoms + a.maxa;
     int32_t *kept = nbk + a.maxa * a.dmax;
@@ -462,11 +466,16 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
     }
 }
 
-template <typename T, int B>
-size_t local_smem(int maxa, int dmax, int max_kept, int nz, bool has_s) {
-    const int NV = has_s ? 8 : 3;
-    return (size_t)NV * maxa * B * sizeof(cpx<T>) + (size_t)nz * sizeof(ShiftL) + (size_t)maxa * 4 +
-           (size_t)maxa * dmax * 4 + (size_t)max_kept * 4 + (size_t)maxa * dmax * 2 + (size_t)maxa * 2 + 16;
+// Shared memory of k_local: the subspace vectors (unless they are placed in
+// global memory), the per-shift states and the local block structure.
+inline size_t local_vec_bytes(int maxa, int b, size_t cpx_size, bool has_s) {
+    return (size_t)(has_s ? 8 : 3) * maxa * b * cpx_size;
+}
+inline size_t local_smem(int maxa, int dmax, int max_kept, int nz, bool has_s, int b, size_t cpx_size,
+                         bool vectors) {
+    return (vectors ? local_vec_bytes(maxa, b, cpx_size, has_s) : 0) + (size_t)nz * sizeof(ShiftL) +
+           (size_t)maxa * 4 + (size_t)maxa * dmax * 4 + (size_t)max_kept * 4 + (size_t)maxa * dmax * 2 +
+           (size_t)maxa * 2 + 16;
 }
 
 struct LocalLaunch {
@@ -482,7 +491,7 @@ struct LocalLaunch {
         LocalArgs<T> a;
         static_assert(sizeof(LocalArgs<T>) == sizeof(LocalArgs<double>), "layout");
         std::memcpy(&a, &args, sizeof(a));
-        const size_t sm = local_smem<T, B>(a.maxa, a.dmax, a.max_kept, a.nz, has_s);
+        const size_t sm = local_smem(a.maxa, a.dmax, a.max_kept, a.nz, has_s, B, sizeof(cpx<T>), a.gvec == nullptr);
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -93,12 +93,19 @@ __device__ __forceinline__ void ld_block(const T *__restrict__ blk, T (&a)[B * B
 }
 
 // acc[i][c] = sum over the blocks of block row br of A_blk(i, j) * v(col*B + j)[c],
-// where v(row) is produced by the loader functor `ld(row, x)`.
-template <typename T, int B, class Loader>
+// where v(row) is produced by the loader functor `ld(row, x)`.  The operand
+// type X is T, or float for df matrices times an FP32 panel (the products and
+// sums stay df).  unit_row = br declares the diagonal block of this row to be
+// the identity (an overlap matrix of orthonormal on-site orbitals): its
+// products are replaced by additions of the operand, which gives the same bits
+// (products with 1 and 0 are exact, and adding an exact zero changes nothing).
+template <typename T, int B, typename X = T, class Loader>
 __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                 const T *__restrict__ val, int64_t br, Loader &ld,
-                                                cpx<T> (&acc)[B][PanelVec<T>::CPT]) {
+                                                cpx<T> (&acc)[B][PanelVec<T>::CPT], int64_t unit_row = -1) {
     constexpr int CPT = PanelVec<T>::CPT;
+    static_assert(std::is_same<X, T>::value || (std::is_same<T, df>::value && std::is_same<X, float>::value),
+                  "operand type");
     const int64_t k0 = __ldg(rp + br), k1 = __ldg(rp + br + 1);
     if constexpr (std::is_same<T, df>::value) {
         DfSum sr[B], si[B];
@@ -107,9 +114,17 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
 #pragma unroll(B <= 4 ? 2 : 1)
         for (int64_t k = k0; k < k1; ++k) {
             const int64_t col = __ldg(ci + k);
-            cpx<T> x[B][CPT];
+            cpx<X> x[B][CPT];
 #pragma unroll
             for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
+            if (col == unit_row) {
+#pragma unroll
+                for (int i = 0; i < B; ++i) {
+                    sr[i].add_val(x[i][0].re);
+                    si[i].add_val(x[i][0].im);
+                }
+                continue;
+            }
             T a[B * B];
             ld_block<T, B>(val + k * (int64_t)(B * B), a);
 #pragma unroll
@@ -134,6 +149,16 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
             cpx<T> x[B][CPT];
 #pragma unroll
             for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
+            if (col == unit_row) {
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) {
+                        acc[i][c].re = acc[i][c].re + x[i][c].re;
+                        acc[i][c].im = acc[i][c].im + x[i][c].im;
+                    }
+                continue;
+            }
             T a[B * B];
             ld_block<T, B>(val + k * (int64_t)(B * B), a);
 #pragma unroll

@@ -116,6 +116,31 @@ def test_local_df64_matches_oracle(ctx):
         assert rel_err_per_shift(G[optr[c]:optr[c + 1]], ref_lu[c]).max() < 1e-9
 
 
+@pytest.mark.parametrize("spec,radii,precision", [
+    (scaled(C3_SYSTEM, n_sites=20000, bdim=9), (5,), tb.TB_PREC_DF64),   # 3 vectors x 560 atoms x 9 x 16 B
+    (scaled(C5_SYSTEM, L=16), (7,), tb.TB_PREC_FP64),                   # 8 vectors x 575 atoms x 4 x 16 B
+], ids=["fcc_b9_r5_df64", "sc_r7_overlap_fp64"])
+def test_local_vectors_beyond_shared_memory(ctx, spec, radii, precision):
+    """Subspaces whose vectors exceed one CTA's shared memory run with the
+    vectors in a global workspace; results as the oracle's COCG."""
+    o, rows, rad, sptr, satoms, rl, optr, orows = _local_case(spec, 3, radii, kept="diag")
+    b = spec.bdim
+    nv = 3 if o.S is None else 8
+    assert nv * np.diff(sptr).max() * b * 16 > 232448          # does not fit 227 KB
+    z = midpoint_shifts(4, -6.0, 6.0, 0.1)
+    res = tb.solve_local(ctx, _bsr(o.H), None if o.S is None else _bsr(o.S), z, rows, sptr, satoms, optr, orows,
+                         tol=1e-11, precision=precision)
+    assert res.rc == 0 and np.all(_np(res.status) == tb.TB_COL_CONVERGED)
+    G = _np(res.G)
+    for c, j in enumerate(rows):
+        atoms = satoms[sptr[c]:sptr[c + 1]].astype(np.int64)
+        Hs = subspace.principal_submatrix(o.H, atoms)
+        Ss = None if o.S is None else subspace.principal_submatrix(o.S, atoms)
+        jl = int(np.searchsorted(atoms, j // b)) * b + int(j % b)
+        ref = cocg.shifted_cocg(Hs.to_csr(), None if Ss is None else Ss.to_csr(), z, [jl], [0, 1], [jl], tol=1e-12)
+        assert rel_err_per_shift(G[optr[c]:optr[c + 1]], ref.G).max() < 1e-9
+
+
 def test_local_order_does_not_change_results(ctx):
     o, rows, rad, sptr, satoms, rl, optr, orows = _local_case(scaled(C5_SYSTEM, L=10), 30, (1, 2, 3))
     z = midpoint_shifts(6, -8.0, 6.0, 0.1)
