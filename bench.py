@@ -135,9 +135,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def kernel_traffic(kernel: str) -> int | None:
+def kernel_traffic(kernel: str, precision: str = "df64", W: int = 32) -> int | None:
     """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
-    path = os.path.join(ROOT, "profiles", "solver_kernels_c2_df64_w16.md")
+    path = os.path.join(ROOT, "profiles", f"solver_kernels_c2_{precision}_w{W}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -162,9 +162,9 @@ def algorithmic_bytes(n_rows, nnzb, bdim, n_brows, W, n_z, n_ent, esz, dsz):
     return {
         "A_outer_H_product": (7 + hp) * V + Mb + 2 * proj,  # R, P_old, RT, SP, HP in; P, SP, U, HP out; p^m rw
         "B_update": 6 * V + Mb + 3 * proj,              # RT, U, R in; RT, R', T out; S; x^m rw, p^m in
-        "IC_A_inner_S_product": 4 * V + 2 * Vd + Mb,    # T, D_old, Y in; D, A, Y out; S
-        "IC_B_inner_update": 3 * V,                     # T, A in; T out
-        "C_rho": 3 * V + Vd,                            # R, D, RT in; R out
+        "IC_A_inner_S_product": 2 * V + 2 * Vd + Mb,    # T, D_old in; D, A out; S
+        "IC_B_inner_update": 5 * V + Vd,                # Y, D, T, A in; Y, T out
+        "C_rho": 2 * V,                                 # R, RT in
     }
 
 
@@ -197,13 +197,32 @@ def df_ops(n_rows, nnzb, bdim, W, s_unit=True):
     alg = {
         "A_outer_H_product": prod_h + own * (4 * cx_axpy + dot),     # p, Sp, Hp, u; mu
         "B_update": prod_s + own * (4 + cx_axpy + 2 * DF_ADD + 2 * norm),
-        "IC_A_inner_S_product": prod_s + own * (2 + 2 * DF_FMA_F + 2 * (DF_MUL_F + ACC_ADD)),
-        "IC_B_inner_update": own * (2 * DF_FMA + norm),
-        "C_rho": own * (2 * DF_FMA_F + dot),
+        "IC_A_inner_S_product": prod_s + own * (2 + 2 * (DF_MUL_F + ACC_ADD)),
+        "IC_B_inner_update": own * (2 * DF_FMA_F + 2 * DF_FMA + norm),
+        "C_rho": own * dot,
     }
     extra = {"B_update": nb * 4, "IC_A_inner_S_product": nb * 2}
     impl = {k: v + extra.get(k, 0) for k, v in alg.items()}
     return alg, impl
+
+
+def spmm_bandwidth(tb, ctx, H, Hh, peaks) -> dict:
+    """The metric's second figure: the block-sparse product H P alone (tb_bsr_spmm_profile, cold L2 per launch).
+
+    Algorithmic bytes: the matrix once (values in the working precision,
+    column indices, row pointers) + the panel read once + the product written
+    once; achieved = bytes / kernel time against the measured HBM copy peak."""
+    out = {}
+    for name, prec, W, esz in (("fp32_w64", tb.TB_PREC_MIXED, 64, 4), ("df64_w32", tb.TB_PREC_DF64, 32, 8),
+                               ("fp64_w32", tb.TB_PREC_FP64, 32, 8)):
+        ms = tb.spmm_profile(ctx, H, W, prec, reps=10)
+        nbytes = (Hh.nnzb * Hh.bdim ** 2 * esz + Hh.nnzb * 4 + (Hh.n_brows + 1) * 8
+                  + 2 * Hh.n_rows * W * 2 * esz)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes": nbytes, "achieved_gbs": gbs, "frac": gbs / peaks["hbm_gbs"]}
+    out["peak_gbs"] = peaks["hbm_gbs"]
+    out["note"] = "H (C2, 229,376 4x4 blocks) times a complex panel; L2 flushed before every timed launch"
+    return out
 
 
 def unit_diagonal(S) -> bool:
@@ -370,16 +389,17 @@ def run_ours(args, rank, world):
                 "op_definition": "FP32 instructions of the df arithmetic with every vector element formed once "
                                  "(one per lane per clock); peak = 152 SMs x 128 FP32 lanes x 2.07 GHz",
                 "ops_per_launch": ops[dom], "ops_per_launch_implemented": ops_impl[dom],
-                "traffic": kernel_traffic(dom), "hbm": hbm}
+                "traffic": kernel_traffic(dom, args.precision, W), "hbm": hbm}
     else:
         roof = {"bound": "alu" if prec == tb.TB_PREC_FP64 else "hbm", "kernel": dom, **hbm,
-                "traffic": kernel_traffic(dom)}
+                "traffic": kernel_traffic(dom, args.precision, W)}
     roof.update({"ms_per_launch": prof[dom], "per_kernel_ms": prof,
                  "per_kernel_share": {k: share[k] / sum(share.values()) for k in share},
                  "per_kernel_gbs": {k: algo[k] / (prof[k] * 1e-3) / 1e9 for k in prof if prof[k] > 0}})
+    spmm = spmm_bandwidth(tb, ctx, H, Hh, peaks) if rank == 0 else None
     ctx.close()
     return {"value": value, "ms": ms_max, "pairs": pairs_all, "launches": launches_all, "clocks": clk.summary(),
-            "e2e": e2e, "roofline": roof, "outer_iters": outer, "inner_iters": inner, "fp64": fp64,
+            "e2e": e2e, "roofline": roof, "spmm": spmm, "outer_iters": outer, "inner_iters": inner, "fp64": fp64,
             "iters_per_column": [int(x) for r in results for x in (r.iters.cpu().numpy() if hasattr(r.iters, "cpu")
                                                                     else r.iters)]}
 
@@ -529,10 +549,10 @@ def cpu_oracle_sample(target_seconds: float, iters_needed: float | None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--panel-w", type=int, default=16)
+    ap.add_argument("--panel-w", type=int, default=32)
     ap.add_argument("--precision", default="df64", choices=["df64", "mixed", "fp64"])
     ap.add_argument("--kernel-profile", action="store_true",
                     help="only launch the solver kernels of one panel (CUDA events; for ncu captures)")
@@ -605,7 +625,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": {"mixed": "f32+f64", "df64": "df64 (f32 pairs)+f64", "fp64": "f64"}[args.precision],
             "data": "synthetic", "config": workload_config(args.panel_w, args.precision, args.gpus),
             "clocks": out["clocks"], "e2e": out["e2e"], "gpu_launches": int(out["launches"]),
-            "roofline": out["roofline"], "cpu_baseline": cpu,
+            "roofline": out["roofline"], "spmm_hbm": out["spmm"], "cpu_baseline": cpu,
             "solver": {"outer_iters": out["outer_iters"], "inner_iters": out["inner_iters"],
                        "mean_iters_per_column": float(np.mean(out["iters_per_column"]))},
             "plain_fp64": out["fp64"]}

@@ -155,6 +155,17 @@ int tb_build_csr(const tb_system_spec *spec, uint64_t seed, tb_bsr *H, tb_bsr *S
 int tb_bsr_spmm(tb_ctx *ctx, const tb_bsr *A, const double *X, int32_t ncols, double *Y,
                 int32_t precision, void *stream);
 
+/* Time the block-sparse product kernel of tb_bsr_spmm alone: the matrix is
+ * converted and a panel of width panel(ncols) in the working precision is
+ * filled once with test values in the library's workspace; then one untimed
+ * launch and `reps` launches, each between CUDA events on `stream` after a
+ * 256 MB write that evicts the operands from L2 (cold-L2 time).
+ * *ms_per_launch = average milliseconds per product (the measurement behind
+ * the SpMM bandwidth figure; Sec. 3's shared product).  Allocates only the
+ * context's workspace; TB_ERR_ARG / TB_ERR_UNSUPPORTED as tb_bsr_spmm. */
+int tb_bsr_spmm_profile(tb_ctx *ctx, const tb_bsr *A, int32_t ncols, int32_t precision, int32_t reps,
+                        void *stream, double *ms_per_launch);
+
 /* ------------------------------------------------------ shifted COCG solve */
 typedef struct {
     double tol;          /* stop a shift when ||b - (zS-H)x|| <= tol ||b|| (recurrence

@@ -8,6 +8,7 @@ not been built, every call raises: there is no CPU fallback.
 
   build_system(spec, seed)            synthetic H, S                   (tb_build_bsr)
   bsr_spmm(ctx, A, X)                 Y = A X, complex panel           (tb_bsr_spmm)
+  spmm_profile(ctx, A, ncols, prec)   ms per product kernel launch     (tb_bsr_spmm_profile)
   solve(ctx, H, S, z, rhs, optr, orows, ...)
                                       G_ij(z) = e_i^T (zS-H)^{-1} e_j  (shifted_cocg_solve)
   reduce_ldos_dm(ctx, G, z, ...)      LDOS and DM elements              (gf_reduce_ldos_dm)
@@ -24,7 +25,7 @@ from . import _lib
 from ._lib import (TB_COL_BREAKDOWN, TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_NONFINITE, TB_PREC_DF64,
                    TB_PREC_FP64, TB_PREC_MIXED)
 
-__all__ = ["Context", "Bsr", "TbError", "build_system", "bsr_spmm", "solve", "profile", "reduce_ldos_dm",
+__all__ = ["Context", "Bsr", "TbError", "build_system", "bsr_spmm", "spmm_profile", "solve", "profile", "reduce_ldos_dm",
            "spec_to_c", "local_subspaces", "solve_local", "descriptors", "mlp_grad", "mlp_train", "mlp_predict",
            "mlp_param_count",
            "TB_PREC_FP64", "TB_PREC_MIXED", "TB_PREC_DF64", "TB_COL_CONVERGED", "TB_COL_MAX_ITER", "TB_COL_BREAKDOWN",
@@ -220,6 +221,16 @@ def bsr_spmm(ctx: Context, A: Bsr, X, precision: int = TB_PREC_FP64):
     rc = ctx.lib.tb_bsr_spmm(ctx.h, ctypes.byref(Ac), _ptr(Xc), ncols, _ptr(Y), precision, _stream_of(A.val))
     ctx.check(rc, "tb_bsr_spmm")
     return Y
+
+
+def spmm_profile(ctx: Context, A: Bsr, ncols: int, precision: int = TB_PREC_FP64, reps: int = 20) -> float:
+    """Average milliseconds of one product kernel launch (tb_bsr_spmm_profile)."""
+    ms = ctypes.c_double(0.0)
+    Ac = A.c_struct()
+    rc = ctx.lib.tb_bsr_spmm_profile(ctx.h, ctypes.byref(Ac), int(ncols), int(precision), int(reps),
+                                     _stream_of(A.val), ctypes.byref(ms))
+    ctx.check(rc, "tb_bsr_spmm_profile")
+    return float(ms.value)
 
 
 @dataclass

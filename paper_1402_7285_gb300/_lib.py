@@ -63,6 +63,8 @@ SIGNATURES = {
     "tb_build_bsr": (ctypes.c_int, [PS, ctypes.c_uint64, PB, PB, ctypes.POINTER(ctypes.c_uint64)]),
     "tb_build_csr": (ctypes.c_int, [PS, ctypes.c_uint64, PB, PB, ctypes.POINTER(ctypes.c_uint64)]),
     "tb_bsr_spmm": (ctypes.c_int, [P, PB, P, ctypes.c_int32, P, ctypes.c_int32, P]),
+    "tb_bsr_spmm_profile": (ctypes.c_int, [P, PB, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
+                                           ctypes.POINTER(ctypes.c_double)]),
     "tb_solve_opts_default": (None, [PO]),
     "shifted_cocg_solve": (ctypes.c_int, [P, PB, PB, P, ctypes.c_int32, P, ctypes.c_int64, P, P, PO, P, P, P,
                                           P]),

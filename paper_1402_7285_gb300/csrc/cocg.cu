@@ -195,6 +195,12 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const int per_sm = opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 3;
     int ncta = (int)std::min<int64_t>((int64_t)per_sm * num_sms(), (H->n_brows + per_cta - 1) / per_cta);
     if (ncta < 1) ncta = 1;
+    // IC_A is compiled for four resident CTAs per SM (block edges <= 4): one more than the rest
+    int ncta_a = ncta;
+    if (b <= 4 && per_sm < 4)
+        ncta_a = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(per_sm + 1) * num_sms(),
+                                                             (H->n_brows + per_cta - 1) / per_cta));
+    const int ncta_max = std::max(ncta, ncta_a);
     void *vec_base = nullptr;
     rc = ws_get(ctx, WS_SOLVE_VEC, vec_bytes * n_vec, &vec_base);
     if (rc) return rc;
@@ -207,7 +213,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const size_t o_col = take(sizeof(ColState) * W);
     const size_t o_sh = take(sizeof(ShiftState) * (size_t)W * n_z);
     const size_t o_ctl = take(sizeof(Ctrl));
-    const size_t o_part = take(sizeof(double) * (size_t)W * 4 * ncta);
+    const size_t o_part = take(sizeof(double) * (size_t)W * 4 * ncta_max);
     const size_t o_zc = take(sizeof(c64) * n_z);
     const size_t o_prow = take(sizeof(int64_t) * pan_row.size());
     const size_t o_pdst = take(sizeof(int64_t) * pan_dst.size());
@@ -308,6 +314,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
 
     SolveLaunch L{ctx, has_s, ncta, n_rows, n_panels, stream, profile_reps, ms};
     L.pd = p;
+    L.ncta_a = ncta_a;
     const bool launched = opts.precision == TB_PREC_FP64    ? launch_panel_f64(L, b, W)
                           : opts.precision == TB_PREC_MIXED ? launch_panel_f32(L, b, W)
                                                             : launch_panel_df(L, b, W);

@@ -237,9 +237,8 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
     Acc<T> acc[CPT][2];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
+    const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
+    for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
         cpx<T> y[B][CPT];
         if constexpr (HP_REC)
             bsr_row_product<T, B>(p.h_rp, p.h_ci, p.h_val, br, lr, y);
@@ -364,9 +363,8 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_sI(Panel<T> p) 
     Acc<T> acc[CPT][3];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero(), acc[cc][2].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
+    const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
+    for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int64_t row = br * B + i;
@@ -425,9 +423,8 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
     Acc<T> acc[CPT][2];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
+    const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
+    for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
         cpx<T> sy[B][CPT];
         bsr_row_product<T, B, X>(p.s_rp, p.s_ci, p.s_val, br, ld, sy, p.s_unit ? br : -1);
 #pragma unroll
@@ -486,7 +483,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
 
 // ------------------------------------------------------- inner CG on S: IC_A
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_a(Panel<T> p) {
+__global__ void __launch_bounds__(NT, (B <= 4 ? 4 : 1)) k_inner_a(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -497,21 +494,13 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_a(Panel<T> p) {
     ld.t = p.Tv;
     ld.d = (k == 0) ? nullptr : p.D[(k + 1) & 1];
     ld.lane = lane;
-    // the previous iteration's solution update y += alpha_{k-1} d_{k-1}, due
-    // here (the step length is known and d_{k-1} is read anyway)
-    T *Y = p.R[(p.ctl->n + 1) & 1];
-    T ya[CPT];
 #pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) {
-        ld.s[cc] = (X)p.col[lane * CPT + cc].in_beta;
-        ya[cc] = (T)p.col[lane * CPT + cc].in_alpha;
-    }
+    for (int cc = 0; cc < CPT; ++cc) ld.s[cc] = (X)p.col[lane * CPT + cc].in_beta;
     Acc<T> acc[CPT][1];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
+    const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
+    for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
         cpx<T> sd[B][CPT];
         bsr_row_product<T, B, X>(p.s_rp, p.s_ci, p.s_val, br, ld, sd, p.s_unit ? br : -1);
 #pragma unroll
@@ -521,18 +510,6 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_a(Panel<T> p) {
             ld(row, d);
             st_dir<T, W>(Dn, row, lane, d);
             st_row<T, W>(p.Av, row, lane, sd[i]);
-            if (ld.d) {
-                cpx<T> y[CPT];
-                cpx<X> dp[CPT];
-                ld_row<T, W>(Y, row, lane, y);
-                ld_dir<T, W>(ld.d, row, lane, dp);
-#pragma unroll
-                for (int cc = 0; cc < CPT; ++cc) {
-                    y[cc].re = fma_x(ya[cc], dp[cc].re, y[cc].re);
-                    y[cc].im = fma_x(ya[cc], dp[cc].im, y[cc].im);
-                }
-                st_row<T, W>(Y, row, lane, y);
-            }
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
                 acc[cc][0].add(mul_x(sd[i][cc].re, d[cc].re));
@@ -566,28 +543,41 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
+    typedef typename DirOf<T>::type X;
+    const int k = p.ctl->k;
+    const X *D = p.D[k & 1];
+    T *Y = p.R[(p.ctl->n + 1) & 1];
     T a[CPT]; // inner CG step length (real)
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) a[cc] = (T)p.col[lane * CPT + cc].in_alpha;
     Acc<T> acc[CPT][1];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
+    const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
+    for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
+        // all loads of the block row first: 4B independent loads in flight
+        cpx<T> y[B][CPT], t[B][CPT], av[B][CPT];
+        cpx<X> d[B][CPT];
 #pragma unroll
         for (int i = 0; i < B; ++i) {
-            const int64_t row = br * B + i;
-            cpx<T> t[CPT], av[CPT];
-            ld_row<T, W>(p.Tv, row, lane, t);
-            ld_row<T, W>(p.Av, row, lane, av);
+            ld_row<T, W>(Y, br * B + i, lane, y[i]);
+            ld_dir<T, W>(D, br * B + i, lane, d[i]);
+            ld_row<T, W>(p.Tv, br * B + i, lane, t[i]);
+            ld_row<T, W>(p.Av, br * B + i, lane, av[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
-                t[cc] = t[cc] - a[cc] * av[cc];
-                acc[cc][0].add(t[cc].re * t[cc].re);
-                acc[cc][0].add(t[cc].im * t[cc].im);
+                y[i][cc].re = fma_x(a[cc], d[i][cc].re, y[i][cc].re);
+                y[i][cc].im = fma_x(a[cc], d[i][cc].im, y[i][cc].im);
+                t[i][cc].re = fma_x(-a[cc], av[i][cc].re, t[i][cc].re);
+                t[i][cc].im = fma_x(-a[cc], av[i][cc].im, t[i][cc].im);
+                acc[cc][0].add(t[i][cc].re * t[i][cc].re);
+                acc[cc][0].add(t[i][cc].im * t[i][cc].im);
             }
-            st_row<T, W>(p.Tv, row, lane, t);
+            st_row<T, W>(Y, br * B + i, lane, y[i]);
+            st_row<T, W>(p.Tv, br * B + i, lane, t[i]);
         }
     }
     cta_partials<T, W, NT, 1>(acc, p.part);
@@ -624,35 +614,23 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_rho(Panel<T> p, int in
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
-    typedef typename DirOf<T>::type X;
     const int n = p.ctl->n;
-    T *Rn = p.R[(n + 1) & 1];
-    // the inner CG's last solution update, r_{n+1} += alpha d (alpha = 0 for
-    // columns whose update was already applied, and when no inner step ran)
-    const X *Dl = p.D[(p.ctl->k + 1) & 1];
-    T ya[CPT];
-#pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) ya[cc] = (T)p.col[lane * CPT + cc].in_alpha;
+    const T *Rn = p.R[(n + 1) & 1];
     Acc<T> acc[CPT][2];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero();
-    int64_t r0, r1;
-    cta_rows(p.n_brows, blockIdx.x, gridDim.x, r0, r1);
-    for (int64_t br = r0 + team; br < r1; br += TM::PER_CTA) {
+    const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
+    for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
+        cpx<T> rb[B][CPT], rtb[B][CPT];
 #pragma unroll
         for (int i = 0; i < B; ++i) {
-            const int64_t row = br * B + i;
-            cpx<T> r[CPT], rt[CPT];
-            cpx<X> dl[CPT];
-            ld_row<T, W>(Rn, row, lane, r);
-            ld_dir<T, W>(Dl, row, lane, dl);
+            ld_row<T, W>(Rn, br * B + i, lane, rb[i]);
+            ld_row<T, W>(p.RT, br * B + i, lane, rtb[i]);
+        }
 #pragma unroll
-            for (int cc = 0; cc < CPT; ++cc) {
-                r[cc].re = fma_x(ya[cc], dl[cc].re, r[cc].re);
-                r[cc].im = fma_x(ya[cc], dl[cc].im, r[cc].im);
-            }
-            st_row<T, W>(Rn, row, lane, r);
-            ld_row<T, W>(p.RT, row, lane, rt);
+        for (int i = 0; i < B; ++i) {
+            const cpx<T>(&r)[CPT] = rb[i];
+            const cpx<T>(&rt)[CPT] = rtb[i];
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
                 acc[cc][0].add(r[cc].re * rt[cc].re);
@@ -762,6 +740,7 @@ struct SolveLaunch {
     int profile_reps; // > 0: time the kernels of the first panel instead of solving
     double *ms_out;   // [8] average ms per launch (profile)
     Panel<double> pd; // type-erased panel (all T-dependent members are pointers)
+    int ncta_a = 0;   // grid of IC_A (0: ncta); IC_A fits one more CTA per SM
     int rc = TB_OK;
 
     int vec_grid(int W) const {
@@ -782,13 +761,13 @@ struct SolveLaunch {
     template <typename T, int B, int W>
     void profile(Panel<T> p) {
         p.in_graph = 0;
-        const dim3 grid(ncta), block(NT);
+        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta);
         const int has_s_i = has_s ? 1 : 0;
         k_init_state<T, W><<<1, NT, 0, stream>>>(p, has_s_i);
         k_init_vec<T, W><<<vec_grid(W), NT, 0, stream>>>(p, n_rows, has_s_i);
         if (has_s) {
             k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
-            k_inner_a<T, B, W><<<grid, block, 0, stream>>>(p);
+            k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
             k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
             k_rho<T, B, W><<<grid, block, 0, stream>>>(p, 1);
         }
@@ -812,10 +791,10 @@ struct SolveLaunch {
             if (has_s) {
                 // first inner iteration (no previous direction) untimed; time a
                 // steady-state one (k = 1), as most inner iterations of a solve are
-                k_inner_a<T, B, W><<<grid, block, 0, stream>>>(p);
+                k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
                 k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
                 cudaEventRecord(ev[3], stream);
-                k_inner_a<T, B, W><<<grid, block, 0, stream>>>(p);
+                k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
                 cudaEventRecord(ev[4], stream);
                 k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
                 cudaEventRecord(ev[5], stream);
@@ -853,7 +832,7 @@ struct SolveLaunch {
         }
         p.h_outer = gb.handle(g, 1u, cudaGraphCondAssignDefault);
         cudaGraphConditionalHandle h_inner_init = has_s ? gb.handle(g, 0u, 0u) : 0;
-        const dim3 grid(ncta), block(NT);
+        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta);
         int has_s_i = has_s ? 1 : 0;
         int init1 = 1, init0 = 0;
         int64_t nr = n_rows;
@@ -871,7 +850,7 @@ struct SolveLaunch {
             cudaGraph_t ib = nullptr;
             last = gb.add_while(g, h_inner_init, &last, 1, &ib);
             if (!gb.rc) {
-                cudaGraphNode_t x = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid, block, a_pinit, nullptr, 0);
+                cudaGraphNode_t x = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid_a, block, a_pinit, nullptr, 0);
                 gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_pinit, &x, 1);
             }
             last = gb.add_kernel(g, (const void *)k_rho<T, B, W>, grid, block, a_pinit_rho, &last, 1);
@@ -889,7 +868,7 @@ struct SolveLaunch {
                 cudaGraph_t ib = nullptr;
                 x = gb.add_while(ob, p_body.h_inner, &x, 1, &ib);
                 if (!gb.rc) {
-                    cudaGraphNode_t y = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid, block, a_body, nullptr, 0);
+                    cudaGraphNode_t y = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid_a, block, a_body, nullptr, 0);
                     gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_body, &y, 1);
                 }
                 gb.add_kernel(ob, (const void *)k_rho<T, B, W>, grid, block, a_body_rho, &x, 1);

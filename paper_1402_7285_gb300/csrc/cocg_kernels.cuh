@@ -15,11 +15,9 @@
 //       last CTA: beta_n, iteration count, loop condition.
 //   B': (S != I) rt_{n+1} = rt_n - alpha_n u; y_0 = r_n - alpha_n u;
 //       t_0 = rt_{n+1} - S y_0 (one BSR product with S); shifted updates as B;
-//       then the inner CG on S: IC_A (y += a_prev d_prev, d = t + b d,
-//       a = S d, d^H a) and IC_B (t -= a a, t^H t), repeated in a device-side
-//       loop (each solution update is applied one step late, by the next IC_A
-//       or by C, which reads d_prev anyway);
-//   C : r_{n+1} = y += a_last d_last; rho_{n+1} = r_{n+1}^T rt_{n+1}; last CTA as in B.
+//       then the inner CG on S: IC_A (d = t + b d, a = S d, d^H a) and
+//       IC_B (y += a d, t -= a a, t^H t), repeated in a device-side loop;
+//   C : rho_{n+1} = r_{n+1}^T rt_{n+1}; last CTA as in B.
 // All recurrence scalars are FP64.  The loop runs as CUDA-graph conditional
 // WHILE nodes whose conditions the last CTA of B / C / IC_B sets; every loop
 // has a hard iteration cap, so the device loop always ends.
@@ -330,6 +328,7 @@ __device__ __forceinline__ double mul_x(double a, double b) { return a * b; }
 __device__ __forceinline__ df fma_x(df a, float b, df c) { return fma_f(a, b, c); }
 __device__ __forceinline__ float fma_x(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_x(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ df fma_x(df a, df b, df c) { return fma(a, b, c); }
 
 // Inner CG direction d_k = t_k + beta d_{k-1} (real beta per column; d_{k-1}
 // absent at k = 0), formed in the direction type.

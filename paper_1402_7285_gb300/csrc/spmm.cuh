@@ -111,9 +111,13 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
         DfSum sr[B], si[B];
 #pragma unroll
         for (int i = 0; i < B; ++i) sr[i].zero(), si[i].zero();
+        int64_t col_n = k0 < k1 ? (int64_t)__ldg(ci + k0) : 0;
 #pragma unroll(B <= 4 ? 2 : 1)
         for (int64_t k = k0; k < k1; ++k) {
-            const int64_t col = __ldg(ci + k);
+            // the next block's column is loaded a block ahead, so the operand
+            // loads never wait for an index load
+            const int64_t col = col_n;
+            if (k + 1 < k1) col_n = __ldg(ci + k + 1);
             cpx<X> x[B][CPT];
 #pragma unroll
             for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
@@ -123,17 +127,17 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
                     sr[i].add_val(x[i][0].re);
                     si[i].add_val(x[i][0].im);
                 }
-                continue;
+            } else {
+                T a[B * B];
+                ld_block<T, B>(val + k * (int64_t)(B * B), a);
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+#pragma unroll
+                    for (int j = 0; j < B; ++j) {
+                        sr[i].add_prod(a[i * B + j], x[j][0].re);
+                        si[i].add_prod(a[i * B + j], x[j][0].im);
+                    }
             }
-            T a[B * B];
-            ld_block<T, B>(val + k * (int64_t)(B * B), a);
-#pragma unroll
-            for (int i = 0; i < B; ++i)
-#pragma unroll
-                for (int j = 0; j < B; ++j) {
-                    sr[i].add_prod(a[i * B + j], x[j][0].re);
-                    si[i].add_prod(a[i * B + j], x[j][0].im);
-                }
         }
 #pragma unroll
         for (int i = 0; i < B; ++i) acc[i][0] = mk(sr[i].value(), si[i].value());
@@ -143,9 +147,11 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
 #pragma unroll
             for (int c = 0; c < CPT; ++c) acc[i][c] = mk<T>(0, 0);
         // two blocks per trip keep twice the neighbour loads in flight (small blocks)
+        int64_t col_n = k0 < k1 ? (int64_t)__ldg(ci + k0) : 0;
 #pragma unroll(B <= 4 ? 2 : 1)
         for (int64_t k = k0; k < k1; ++k) {
-            const int64_t col = __ldg(ci + k);
+            const int64_t col = col_n;
+            if (k + 1 < k1) col_n = __ldg(ci + k + 1);
             cpx<T> x[B][CPT];
 #pragma unroll
             for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
@@ -157,19 +163,19 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
                         acc[i][c].re = acc[i][c].re + x[i][c].re;
                         acc[i][c].im = acc[i][c].im + x[i][c].im;
                     }
-                continue;
+            } else {
+                T a[B * B];
+                ld_block<T, B>(val + k * (int64_t)(B * B), a);
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+#pragma unroll
+                    for (int j = 0; j < B; ++j)
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c) {
+                            acc[i][c].re = fma(a[i * B + j], x[j][c].re, acc[i][c].re);
+                            acc[i][c].im = fma(a[i * B + j], x[j][c].im, acc[i][c].im);
+                        }
             }
-            T a[B * B];
-            ld_block<T, B>(val + k * (int64_t)(B * B), a);
-#pragma unroll
-            for (int i = 0; i < B; ++i)
-#pragma unroll
-                for (int j = 0; j < B; ++j)
-#pragma unroll
-                    for (int c = 0; c < CPT; ++c) {
-                        acc[i][c].re = fma(a[i * B + j], x[j][c].re, acc[i][c].re);
-                        acc[i][c].im = fma(a[i * B + j], x[j][c].im, acc[i][c].im);
-                    }
         }
     }
 }
@@ -184,10 +190,10 @@ struct Teams {
     static_assert(NT % TPR == 0, "CTA size must be a multiple of the team size");
 };
 
-// Contiguous block-row range [r0, r1) of CTA `cta` out of `ncta`.
-__device__ __forceinline__ void cta_rows(int64_t n_brows, int cta, int ncta, int64_t &r0, int64_t &r1) {
-    const int64_t per = (n_brows + ncta - 1) / ncta;
-    r0 = (int64_t)cta * per;
-    r1 = r0 + per < n_brows ? r0 + per : n_brows;
-    if (r0 > n_brows) r0 = n_brows;
-}
+// Block-row order of the product kernels: groups of PER_CTA consecutive block
+// rows (one per team) are dealt to the CTAs in turn, group g to CTA g mod
+// grid.  The rows in flight at any moment then form one window that sweeps
+// through the matrix, so the neighbour rows its products read (for a lattice
+// numbered plane by plane, within a plane or two of the window) are still in
+// L2 when the next rows ask for them; contiguous per-CTA ranges would spread
+// the front over the whole vector and overflow L2.
