@@ -558,6 +558,8 @@ def main():
                     help="only launch the solver kernels of one panel (CUDA events; for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=100000)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--spmm-only", action="store_true",
+                    help="only the SpMM bandwidth figure (the product kernel alone, C2's H)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: the metric's configuration (panel solver); c3-c5: localized columns")
     ap.add_argument("--local-cols", type=int, default=2048)
@@ -572,6 +574,17 @@ def main():
     args = ap.parse_args()
     args.precision_given = any(a.startswith("--precision") for a in sys.argv[1:])
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.spmm_only and args.impl == "ours":
+        if int(os.environ.get("RANK", "0")) == 0:
+            import torch
+
+            import paper_1402_7285_gb300 as tb
+            torch.cuda.set_device(0)
+            Hh, _, _ = tb.build_system(WORKLOAD.system, WORKLOAD.seed)
+            ctx = tb.Context()
+            print(json.dumps({"spmm_hbm": spmm_bandwidth(tb, ctx, Hh.to("cuda:0"), Hh, measured_peaks())}))
+            ctx.close()
+        return
     if args.workload != "c2" and args.impl == "ours":
         if int(os.environ.get("RANK", "0")) == 0:
             run_local(args)

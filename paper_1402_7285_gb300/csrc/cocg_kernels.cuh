@@ -257,10 +257,21 @@ __device__ __forceinline__ void reduce_partials(const void *part, double *out) {
     typedef typename Acc<T>::P P;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const P *pp = reinterpret_cast<const P *>(part);
+    const int G = (int)gridDim.x;
     for (int q = warp; q < W * K; q += NT / 32) {
+        const P *row = pp + (int64_t)q * G;
         Acc<T> s;
         s.zero();
-        for (int t = lane; t < (int)gridDim.x; t += 32) s.add(Acc<T>::unpack(__ldcg(pp + (int64_t)q * gridDim.x + t)));
+        int t = lane;
+        // four independent loads in flight per lane (the last CTA runs alone)
+        for (; t + 96 < G; t += 128) {
+            const P a = __ldcg(row + t), b = __ldcg(row + t + 32), c = __ldcg(row + t + 64), d = __ldcg(row + t + 96);
+            s.add(Acc<T>::unpack(a));
+            s.add(Acc<T>::unpack(b));
+            s.add(Acc<T>::unpack(c));
+            s.add(Acc<T>::unpack(d));
+        }
+        for (; t < G; t += 32) s.add(Acc<T>::unpack(__ldcg(row + t)));
         warp_reduce(s);
         if (lane == 0) out[q] = s.value();
     }
