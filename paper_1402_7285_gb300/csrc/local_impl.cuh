@@ -48,6 +48,7 @@ struct LocalArgs {
     unsigned long long *queue;
     unsigned long long *stat; // [2]: outer, inner iterations
     double tol, inner_tol;
+    double stall2; // restart threshold on ||rt||^2 (see the restart below); 0 = never
     int32_t max_iter, inner_max;
     c64 *G;
     int32_t *iters;
@@ -141,7 +142,8 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
     __shared__ int s_col, s_nat, s_jloc, s_nkept, s_nact;
     __shared__ c64 s_rho, s_alpha, s_alpha_prev, s_beta_prev;
     __shared__ double s_rn2, s_in_rr, s_in_alpha, s_in_beta, s_in_tol2;
-    __shared__ int s_status, s_stop, s_in_stop;
+    __shared__ int s_status, s_stop, s_in_stop, s_restarts, s_restart;
+    __shared__ c64 s_zs; // this column's seed shift
 
     const int tid = threadIdx.x;
     c64 *xs = a.scratch + (int64_t)blockIdx.x * 2 * a.max_kept * a.nz;
@@ -217,6 +219,9 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
             s_status = TB_COL_MAX_ITER;
             s_stop = (jloc < 0);
             if (jloc < 0) s_status = TB_COL_BREAKDOWN;
+            s_zs = a.zs;
+            s_restarts = 0;
+            s_restart = 0;
         }
         __syncthreads();
 
@@ -291,20 +296,24 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
         };
 
         int64_t inner_total = 0;
-        if constexpr (HAS_S) {
-            inner_total += inner_solve();
-            Acc<T> rr[2];
-            rr[0].zero(), rr[1].zero();
-            for (int l = tid; l < nrows; l += LNT) {
-                rr[0].add(R[l].re * RT[l].re);
-                rr[0].add(-(R[l].im * RT[l].im));
-                rr[1].add(R[l].re * RT[l].im);
-                rr[1].add(R[l].im * RT[l].re);
+        // r_0 = S^{-1} e_j and rho_0 = r_0^T rt_0 (S != I; rho_0 = 1 when S = I)
+        auto seed_start = [&]() {
+            if constexpr (HAS_S) {
+                inner_total += inner_solve();
+                Acc<T> rr[2];
+                rr[0].zero(), rr[1].zero();
+                for (int l = tid; l < nrows; l += LNT) {
+                    rr[0].add(R[l].re * RT[l].re);
+                    rr[0].add(-(R[l].im * RT[l].im));
+                    rr[1].add(R[l].re * RT[l].im);
+                    rr[1].add(R[l].im * RT[l].re);
+                }
+                cta_sum<T, 2>(rr, red);
+                if (tid == 0) s_rho = mk(red[0], red[1]);
+                __syncthreads();
             }
-            cta_sum<T, 2>(rr, red);
-            if (tid == 0) s_rho = mk(red[0], red[1]);
-            __syncthreads();
-        }
+        };
+        seed_start();
 
         int n = 0;
         for (;; ++n) {
@@ -338,6 +347,60 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
             }
             if (my_act) atomicAdd(&s_nact, my_act);
             __syncthreads();
+            // Restart with a new seed.  Every shift's residual is the seed's
+            // divided by |pi|: a shift much harder than the seed needs the seed
+            // residual far below the tolerance, below what the working
+            // precision carries (df: stalls near 1e-10 relative).  When the seed
+            // residual crosses that level with shifts still active, the column
+            // restarts with the worst active shift as its seed; converged shifts
+            // keep their solutions, active ones start again from zero.
+            if (tid == 0) {
+                s_restart = 0;
+                if (s_nact > 0 && !s_stop && s_rn2 < a.stall2 && s_restarts < 2) {
+                    int mw = -1;
+                    double rw = -1.0;
+                    for (int m = 0; m < a.nz; ++m)
+                        if (shs[m].active && shs[m].resid > rw) rw = shs[m].resid, mw = m;
+                    if (mw >= 0) {
+                        s_zs = a.z[mw];
+                        s_restart = 1;
+                        s_restarts += 1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_restart) {
+                for (int m = tid; m < a.nz; m += LNT) {
+                    ShiftL &sm = shs[m];
+                    if (!sm.active) continue;
+                    sm.pi = sm.pi_prev = sm.pi_next = mk(1.0, 0.0);
+                    sm.resid = 1.0;
+                    for (int k = 0; k < s_nkept; ++k) {
+                        xs[(int64_t)k * a.nz + m] = mk(0.0, 0.0);
+                        ps[(int64_t)k * a.nz + m] = mk(0.0, 0.0);
+                    }
+                }
+                for (int l = tid; l < nrows; l += LNT) {
+                    const cpx<T> e = mk<T>(l == jloc ? (T)1 : (T)0, 0);
+                    RT[l] = e;
+                    P[l] = mk<T>(0, 0);
+                    U[l] = mk<T>(0, 0);
+                    if constexpr (HAS_S) {
+                        R[l] = e;
+                        SP[l] = mk<T>(0, 0);
+                    }
+                }
+                if (tid == 0) {
+                    s_rho = mk(1.0, 0.0);
+                    s_alpha = mk(0.0, 0.0);
+                    s_alpha_prev = mk(1.0, 0.0);
+                    s_beta_prev = mk(0.0, 0.0);
+                    s_rn2 = 1.0;
+                }
+                __syncthreads();
+                seed_start();
+                continue; // the next iteration tests the restarted shifts again
+            }
             if (tid == 0) {
                 if (s_nact == 0 && !s_stop) {
                     s_stop = 1;
@@ -351,7 +414,7 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
             if (s_stop) break;
             // ---- seed step: p, Sp, u = z_s Sp - H p, mu = p^T u
             const cpx<T> beta = cvt<T>(s_beta_prev);
-            const cpx<T> zs = cvt<T>(a.zs);
+            const cpx<T> zs = cvt<T>(s_zs);
             for (int l = tid; l < nrows; l += LNT) {
                 P[l] = R[l] + beta * P[l];
                 if constexpr (HAS_S) SP[l] = RT[l] + beta * SP[l];
@@ -393,7 +456,7 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
             for (int m = tid; m < a.nz; m += LNT) {
                 ShiftL &s = shs[m];
                 if (!s.active) continue;
-                const c64 sig = a.z[m] - a.zs;
+                const c64 sig = a.z[m] - s_zs;
                 const c64 coef = cdiv(al64 * s_beta_prev, s_alpha_prev);
                 const c64 pn = (mk(1.0, 0.0) + al64 * sig) * s.pi + coef * (s.pi - s.pi_prev);
                 const c64 as = cdiv(s.pi, pn) * al64;

@@ -11,6 +11,7 @@ pytestmark = pytest.mark.gpu
 import paper_1402_7285_gb300 as tb
 from oracle import cocg, dense, subspace, systems
 from tests.helpers import out_layout, rel_err_per_shift
+from workloads import shifts_of as wl_shifts
 from workloads import C3_SYSTEM, C4_SYSTEM, C5_SYSTEM, midpoint_shifts, sample_local_rhs, scaled
 
 DEV = "cuda:0"
@@ -139,6 +140,30 @@ def test_local_vectors_beyond_shared_memory(ctx, spec, radii, precision):
         jl = int(np.searchsorted(atoms, j // b)) * b + int(j % b)
         ref = cocg.shifted_cocg(Hs.to_csr(), None if Ss is None else Ss.to_csr(), z, [jl], [0, 1], [jl], tol=1e-12)
         assert rel_err_per_shift(G[optr[c]:optr[c + 1]], ref.G).max() < 1e-9
+
+
+def test_local_df64_restarts_for_shifts_harder_than_the_seed(ctx):
+    """C5-like columns at tol 1e-5 with the C5 shift grid: some shifts (near
+    the p-orbital onsite level) need the seed residual far below what df64
+    carries; the column restarts with the worst shift as its seed.  Every
+    column converges and agrees with the oracle's FP64 COCG."""
+    from workloads import C5
+    spec = scaled(C5_SYSTEM, L=12)
+    o, rows, rad, sptr, satoms, rl, optr, orows = _local_case(spec, 48, (4, 5), kept="diag")
+    z = wl_shifts(C5)
+    res = tb.solve_local(ctx, _bsr(o.H), _bsr(o.S), z, rows, sptr, satoms, optr, orows, tol=1e-5,
+                         precision=tb.TB_PREC_DF64, max_iter=30000)
+    assert np.all(_np(res.status) == tb.TB_COL_CONVERGED)
+    assert np.all(_np(res.resid) <= 1e-5)
+    G = _np(res.G)
+    b = spec.bdim
+    for c in range(0, len(rows), 12):
+        atoms = satoms[sptr[c]:sptr[c + 1]].astype(np.int64)
+        Hs = subspace.principal_submatrix(o.H, atoms)
+        Ss = subspace.principal_submatrix(o.S, atoms)
+        jl = int(np.searchsorted(atoms, rows[c] // b)) * b + int(rows[c] % b)
+        ex = dense.green_lu(Hs.to_dense(), Ss.to_dense(), z, [jl])[[jl], 0, :]
+        assert rel_err_per_shift(G[optr[c]:optr[c + 1]], ex).max() < 1e-4   # the oracle at tol 1e-5: 2e-6..7e-6
 
 
 def test_local_order_does_not_change_results(ctx):
