@@ -217,9 +217,9 @@ extern "C" int shifted_cocg_solve_local(tb_ctx *ctx, const tb_bsr *H, const tb_b
     la.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : std::max(1e-3 * opts.tol, mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13));
     la.max_iter = opts.max_iter;
     la.inner_max = opts.inner_max > 0 ? opts.inner_max : 40;
-    // seed residual below which the working precision no longer carries the
-    // harder shifts (restart with a new seed); FP32 never restarts
-    la.stall2 = opts.precision == TB_PREC_DF64 ? 1e-20 : (opts.precision == TB_PREC_FP64 ? 1e-30 : 0.0);
+    // seed residual below which df64 no longer carries the harder shifts
+    // (restart with a new seed); FP64 converges without, FP32 never gets there
+    la.stall2 = opts.precision == TB_PREC_DF64 ? 1e-20 : 0.0;
     la.G = (c64 *)d_G;
     la.iters = (int32_t *)d_iters;
     la.resid = (double *)d_resid;

@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
     __shared__ int s_col, s_nat, s_jloc, s_nkept, s_nact;
     __shared__ c64 s_rho, s_alpha, s_alpha_prev, s_beta_prev;
     __shared__ double s_rn2, s_in_rr, s_in_alpha, s_in_beta, s_in_tol2;
-    __shared__ int s_status, s_stop, s_in_stop, s_restarts, s_restart;
+    __shared__ int s_status, s_stop, s_in_stop, s_restarts, s_restart, s_chk_n;
+    __shared__ double s_chk_w;
     __shared__ c64 s_zs; // this column's seed shift
 
     const int tid = threadIdx.x;
@@ -222,6 +223,8 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
             s_zs = a.zs;
             s_restarts = 0;
             s_restart = 0;
+            s_chk_n = -1;
+            s_chk_w = 0.0;
         }
         __syncthreads();
 
@@ -350,21 +353,27 @@ __global__ void __launch_bounds__(LNT) k_local(LocalArgs<T> a) {
             // Restart with a new seed.  Every shift's residual is the seed's
             // divided by |pi|: a shift much harder than the seed needs the seed
             // residual far below the tolerance, below what the working
-            // precision carries (df: stalls near 1e-10 relative).  When the seed
-            // residual crosses that level with shifts still active, the column
-            // restarts with the worst active shift as its seed; converged shifts
-            // keep their solutions, active ones start again from zero.
+            // precision carries (df: near 1e-10 relative).  Once the seed
+            // residual is below that level, the worst active shift is checked
+            // every 256 iterations; if it improved by less than 10 % the column
+            // restarts with that shift as its seed: converged shifts keep their
+            // solutions, active ones start again from zero.
             if (tid == 0) {
                 s_restart = 0;
-                if (s_nact > 0 && !s_stop && s_rn2 < a.stall2 && s_restarts < 2) {
+                if (s_nact > 0 && !s_stop && s_rn2 < a.stall2 && s_restarts < 2 &&
+                    (s_chk_n < 0 || n - s_chk_n >= 256)) {
                     int mw = -1;
                     double rw = -1.0;
                     for (int m = 0; m < a.nz; ++m)
                         if (shs[m].active && shs[m].resid > rw) rw = shs[m].resid, mw = m;
-                    if (mw >= 0) {
+                    if (s_chk_n >= 0 && mw >= 0 && rw > 0.9 * s_chk_w) {
                         s_zs = a.z[mw];
                         s_restart = 1;
                         s_restarts += 1;
+                        s_chk_n = -1;
+                    } else {
+                        s_chk_n = n;
+                        s_chk_w = rw;
                     }
                 }
             }
