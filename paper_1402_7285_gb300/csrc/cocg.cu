@@ -195,9 +195,10 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const int per_sm = opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 3;
     int ncta = (int)std::min<int64_t>((int64_t)per_sm * num_sms(), (H->n_brows + per_cta - 1) / per_cta);
     if (ncta < 1) ncta = 1;
-    // IC_A is compiled for four resident CTAs per SM (block edges <= 4): one more than the rest
+    // IC_A, B' and C are compiled for four resident CTAs per SM (df panels, block edges <= 4): one more
+    // than A and IC_B
     int ncta_a = ncta;
-    if (b <= 4 && per_sm < 4)
+    if (b <= 4 && opts.precision == TB_PREC_DF64 && per_sm < 4)
         ncta_a = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(per_sm + 1) * num_sms(),
                                                              (H->n_brows + per_cta - 1) / per_cta));
     const int ncta_max = std::max(ncta, ncta_a);

@@ -101,6 +101,14 @@ __global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
 // kept rows of a column are updated in parallel, not one after another.
 constexpr int PAIR_CHUNK = 128;
 
+// Resident CTAs per SM that IC_A, B' and C are compiled for: four for df
+// panels with block edges <= 4 (64 registers suffice), otherwise the three of
+// the other kernels (the FP64 and FP32 variants would spill at 64).
+template <typename T, int B>
+constexpr int ctas_light() {
+    return B <= 4 ? (std::is_same<T, df>::value ? 4 : 3) : 1;
+}
+
 // A(n): rotate pi, test ||rt_n|| / |pi_n| <= tol, then p^m_n = r_n / pi_n + beta^m_{n-1} p^m_{n-1}.
 template <typename T, int W>
 __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) {
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_sI(Panel<T> p) 
 
 // -------------------------------------------------------------- kernel B' (S != I)
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
+__global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_update_S(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -483,7 +491,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
 
 // ------------------------------------------------------- inner CG on S: IC_A
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, (B <= 4 ? 4 : 1)) k_inner_a(Panel<T> p) {
+__global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_inner_a(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -610,7 +618,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
 
 // -------------------------------------------------------------- kernel C (S != I)
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_rho(Panel<T> p, int init) {
+__global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_rho(Panel<T> p, int init) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -740,7 +748,7 @@ struct SolveLaunch {
     int profile_reps; // > 0: time the kernels of the first panel instead of solving
     double *ms_out;   // [8] average ms per launch (profile)
     Panel<double> pd; // type-erased panel (all T-dependent members are pointers)
-    int ncta_a = 0;   // grid of IC_A (0: ncta); IC_A fits one more CTA per SM
+    int ncta_a = 0;   // grid of IC_A, B' and C (0: ncta): they fit one more CTA per SM than A and IC_B
     int rc = TB_OK;
 
     int vec_grid(int W) const {
@@ -766,10 +774,10 @@ struct SolveLaunch {
         k_init_state<T, W><<<1, NT, 0, stream>>>(p, has_s_i);
         k_init_vec<T, W><<<vec_grid(W), NT, 0, stream>>>(p, n_rows, has_s_i);
         if (has_s) {
-            k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
+            k_update_S<T, B, W><<<grid_a, block, 0, stream>>>(p);
             k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
             k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
-            k_rho<T, B, W><<<grid, block, 0, stream>>>(p, 1);
+            k_rho<T, B, W><<<grid_a, block, 0, stream>>>(p, 1);
         }
         // events: [0] A [1] B [2] (untimed first inner pair) [3] IC_A [4] IC_B [5] C [6]
         cudaEvent_t ev[7];
@@ -783,7 +791,7 @@ struct SolveLaunch {
                 k_outer<T, B, W, false><<<grid, block, 0, stream>>>(p);
             cudaEventRecord(ev[1], stream);
             if (has_s)
-                k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
+                k_update_S<T, B, W><<<grid_a, block, 0, stream>>>(p);
             else
                 k_update_sI<T, B, W><<<grid, block, 0, stream>>>(p);
             cudaEventRecord(ev[2], stream);
@@ -798,7 +806,7 @@ struct SolveLaunch {
                 cudaEventRecord(ev[4], stream);
                 k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
                 cudaEventRecord(ev[5], stream);
-                k_rho<T, B, W><<<grid, block, 0, stream>>>(p, 0);
+                k_rho<T, B, W><<<grid_a, block, 0, stream>>>(p, 0);
                 cudaEventRecord(ev[6], stream);
                 last = 6;
             }
@@ -846,14 +854,14 @@ struct SolveLaunch {
         void *a_pinit[] = {&p_init};
         void *a_pinit_rho[] = {&p_init, &init1};
         if (has_s) {
-            last = gb.add_kernel(g, (const void *)k_update_S<T, B, W>, grid, block, a_pinit, &last, 1);
+            last = gb.add_kernel(g, (const void *)k_update_S<T, B, W>, grid_a, block, a_pinit, &last, 1);
             cudaGraph_t ib = nullptr;
             last = gb.add_while(g, h_inner_init, &last, 1, &ib);
             if (!gb.rc) {
                 cudaGraphNode_t x = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid_a, block, a_pinit, nullptr, 0);
                 gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_pinit, &x, 1);
             }
-            last = gb.add_kernel(g, (const void *)k_rho<T, B, W>, grid, block, a_pinit_rho, &last, 1);
+            last = gb.add_kernel(g, (const void *)k_rho<T, B, W>, grid_a, block, a_pinit_rho, &last, 1);
         }
         cudaGraph_t ob = nullptr;
         cudaGraphNode_t outer = gb.add_while(g, p.h_outer, &last, 1, &ob);
@@ -864,14 +872,14 @@ struct SolveLaunch {
             if (has_s) {
                 p_body.h_inner = gb.handle(ob, 0u, 0u);
                 cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, true>, grid, block, a_body, nullptr, 0);
-                x = gb.add_kernel(ob, (const void *)k_update_S<T, B, W>, grid, block, a_body, &x, 1);
+                x = gb.add_kernel(ob, (const void *)k_update_S<T, B, W>, grid_a, block, a_body, &x, 1);
                 cudaGraph_t ib = nullptr;
                 x = gb.add_while(ob, p_body.h_inner, &x, 1, &ib);
                 if (!gb.rc) {
                     cudaGraphNode_t y = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid_a, block, a_body, nullptr, 0);
                     gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_body, &y, 1);
                 }
-                gb.add_kernel(ob, (const void *)k_rho<T, B, W>, grid, block, a_body_rho, &x, 1);
+                gb.add_kernel(ob, (const void *)k_rho<T, B, W>, grid_a, block, a_body_rho, &x, 1);
             } else {
                 cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, false>, grid, block, a_body, nullptr, 0);
                 gb.add_kernel(ob, (const void *)k_update_sI<T, B, W>, grid, block, a_body, &x, 1);

@@ -4,8 +4,10 @@
 
 namespace {
 
+// FP32 panels: four resident CTAs per SM (64 registers); the product waits on
+// L2, so more warps in flight matter more than the few spilled registers.
 template <typename T, int B, int W, int NT>
-__global__ void __launch_bounds__(NT) k_spmm(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_spmm(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                              const T *__restrict__ val, int64_t n_brows, const T *__restrict__ X,
                                              T *__restrict__ Y) {
     using TM = Teams<T, W, NT>;
