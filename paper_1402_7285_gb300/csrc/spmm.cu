@@ -4,12 +4,10 @@
 
 namespace {
 
-// FP32 panels: four resident CTAs per SM (64 registers); the product waits on
-// L2, so more warps in flight matter more than the few spilled registers.
 template <typename T, int B, int W, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_spmm(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                             const T *__restrict__ val, int64_t n_brows, const T *__restrict__ X,
-                                             T *__restrict__ Y) {
+__device__ __forceinline__ void spmm_rows(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                          const T *__restrict__ val, int64_t n_brows, const T *__restrict__ X,
+                                          T *__restrict__ Y) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -21,6 +19,22 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 1) k_spmm(const int64
 #pragma unroll
         for (int i = 0; i < B; ++i) st_row<T, W>(Y, br * B + i, lane, acc[i]);
     }
+}
+
+template <typename T, int B, int W, int NT>
+__global__ void __launch_bounds__(NT) k_spmm(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                             const T *__restrict__ val, int64_t n_brows, const T *__restrict__ X,
+                                             T *__restrict__ Y) {
+    spmm_rows<T, B, W, NT>(rp, ci, val, n_brows, X, Y);
+}
+
+// FP32 panels: four resident CTAs per SM (64 registers); the product waits on
+// L2, so more warps in flight matter more than the few spilled registers.
+template <int B, int W, int NT>
+__global__ void __launch_bounds__(NT, 4) k_spmm_f32(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                    const float *__restrict__ val, int64_t n_brows,
+                                                    const float *__restrict__ X, float *__restrict__ Y) {
+    spmm_rows<float, B, W, NT>(rp, ci, val, n_brows, X, Y);
 }
 
 // dst[r][0:W] <- src[r][0:ncols] (complex), zero padded; T may be float or double.
@@ -87,7 +101,10 @@ struct SpmmLaunch {
         int64_t need = (n_brows + TM::PER_CTA - 1) / TM::PER_CTA;
         int g = (int)(need < grid ? need : grid);
         if (g < 1) g = 1;
-        k_spmm<T, B, W, NT><<<g, NT, 0, s>>>(rp, ci, (const T *)val, n_brows, (const T *)X, (T *)Y);
+        if constexpr (std::is_same<T, float>::value)
+            k_spmm_f32<B, W, NT><<<g, NT, 0, s>>>(rp, ci, (const float *)val, n_brows, (const float *)X, (float *)Y);
+        else
+            k_spmm<T, B, W, NT><<<g, NT, 0, s>>>(rp, ci, (const T *)val, n_brows, (const T *)X, (T *)Y);
     }
 };
 
