@@ -184,7 +184,7 @@ typedef struct {
     int32_t inner_max;   /* S != I: inner iterations per outer iteration, 0 = 40   */
     int32_t ctas_per_sm; /* resident CTAs per SM for the panel kernels, 0 = 3;
                             with df panels and block edges <= 4 the inner S
-                            product, B' and C run one more (at most 4)        */
+                            product and the rho kernel run one more (at most 4) */
     void *stream;        /* cudaStream_t to queue work on                         */
     int64_t *stats;      /* optional host array [2]: outer and inner iterations
                             summed over all panels (written before returning)     */

@@ -195,8 +195,8 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const int per_sm = opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 3;
     int ncta = (int)std::min<int64_t>((int64_t)per_sm * num_sms(), (H->n_brows + per_cta - 1) / per_cta);
     if (ncta < 1) ncta = 1;
-    // IC_A, B' and C are compiled for four resident CTAs per SM (df panels, block edges <= 4): one more
-    // than A and IC_B
+    // IC_A and C are compiled for four resident CTAs per SM (df panels, block edges <= 4): one more
+    // than the other kernels
     int ncta_a = ncta;
     if (b <= 4 && opts.precision == TB_PREC_DF64 && per_sm < 4)
         ncta_a = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(per_sm + 1) * num_sms(),
@@ -303,6 +303,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.part = sb + o_part;
     p.ctl = (Ctrl *)(sb + o_ctl);
     p.tol = opts.tol;
+    p.stall2 = opts.precision == TB_PREC_DF64 ? 1e-20 : 0.0; // df64 restarts (see k_outer)
     p.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : std::max(1e-3 * opts.tol, mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13));
     p.max_iter = opts.max_iter;
     p.inner_max = opts.inner_max > 0 ? opts.inner_max : 40;

@@ -37,6 +37,8 @@ __global__ void k_init_state(Panel<T> p, int has_s) {
             C.status = TB_COL_CONVERGED;
         }
         C.in_done = 1;
+        C.zs = p.zs;
+        C.chk_n = -1;
         p.col[c] = C;
     }
     for (int q = threadIdx.x; q < W * p.nz; q += blockDim.x) {
@@ -101,7 +103,7 @@ __global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
 // kept rows of a column are updated in parallel, not one after another.
 constexpr int PAIR_CHUNK = 128;
 
-// Resident CTAs per SM that IC_A, B' and C are compiled for: four for df
+// Resident CTAs per SM that IC_A and C are compiled for: four for df
 // panels with block edges <= 4 (64 registers suffice), otherwise the three of
 // the other kernels (the FP64 and FP32 variants would spill at 64).
 template <typename T, int B>
@@ -182,7 +184,7 @@ __device__ void pair_step_B(const Panel<T> &p) {
             ColState &C = p.col[c];
             ShiftState &S = p.sh[q];
             if (!C.done && S.active) {
-                const c64 sig = p.z[m] - p.zs;
+                const c64 sig = p.z[m] - C.zs;
                 const c64 coef = cdiv(C.alpha * C.beta_prev, C.alpha_prev);
                 const c64 pn = (mk(1.0, 0.0) + C.alpha * sig) * S.pi + coef * (S.pi - S.pi_prev);
                 const c64 as = cdiv(S.pi, pn) * C.alpha;
@@ -241,7 +243,9 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
     }
     LdAxpy<T, W> lr = ld; // r_n
     lr.b = nullptr;
-    const cpx<T> zs = cvt<T>(p.zs);
+    cpx<T> zs[CPT]; // each column's seed shift
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) zs[cc] = cvt<T>(p.col[lane * CPT + cc].zs);
     Acc<T> acc[CPT][2];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero();
@@ -272,12 +276,12 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
 #pragma unroll
                 for (int cc = 0; cc < CPT; ++cc) {
                     sp[cc] = rt[cc] + ld.s[cc] * sp[cc];
-                    u[cc] = zs * sp[cc] - y[i][cc];
+                    u[cc] = zs[cc] * sp[cc] - y[i][cc];
                 }
                 st_row<T, W>(p.SP, row, lane, sp);
             } else {
 #pragma unroll
-                for (int cc = 0; cc < CPT; ++cc) u[cc] = zs * pv[cc] - y[i][cc];
+                for (int cc = 0; cc < CPT; ++cc) u[cc] = zs[cc] * pv[cc] - y[i][cc];
             }
             st_row<T, W>(p.U, row, lane, u);
 #pragma unroll
@@ -322,6 +326,49 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
             C.alpha = a;
         }
     }
+    // Restart (df panels): a shift's residual is the seed's divided by |pi|, so
+    // a shift much harder than the seed needs the seed residual below what df
+    // carries (about 1e-10).  Once a column's seed residual is below that, its
+    // worst active shift is checked every 512 iterations; if it improved by
+    // less than 1 % the column restarts with that shift as its seed: alpha = 0
+    // this iteration, B / B' reset rt to e_j, C restarts the recurrences;
+    // converged shifts keep their solutions, active ones start from zero.
+    if (p.stall2 > 0.0) {
+        const int panel = p.ctl->panel;
+        const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
+        for (int c = threadIdx.x; c < W; c += NT) {
+            ColState &C = p.col[c];
+            if (C.done || !(C.rn2 < p.stall2) || C.restarts >= 2) continue;
+            if (C.chk_n >= 0 && C.iters - C.chk_n < 512) continue;
+            double rw = -1.0;
+            int mw = -1;
+            for (int m = 0; m < p.nz; ++m) {
+                const ShiftState &S = p.sh[(int64_t)c * p.nz + m];
+                if (S.active && S.resid > rw) rw = S.resid, mw = m;
+            }
+            if (mw < 0) continue;
+            if (C.chk_n < 0 || rw < 0.99 * C.chk_w) {
+                C.chk_n = C.iters;
+                C.chk_w = rw;
+                continue;
+            }
+            C.zs = p.z[mw];
+            C.restart = 1;
+            C.restarts += 1;
+            C.chk_n = -1;
+            C.alpha = mk(0.0, 0.0);
+            for (int m = 0; m < p.nz; ++m) {
+                ShiftState &S = p.sh[(int64_t)c * p.nz + m];
+                if (!S.active) continue;
+                S.pi = S.pi_prev = S.pi_next = mk(1.0, 0.0);
+                S.resid = 1.0;
+                for (int e = eptr[c]; e < eptr[c + 1]; ++e) {
+                    p.xs[(int64_t)e * p.nz + m] = mk(0.0, 0.0);
+                    p.ps[(int64_t)e * p.nz + m] = mk(0.0, 0.0);
+                }
+            }
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int all = 1;
@@ -339,6 +386,14 @@ __device__ void finish_outer(const Panel<T> &p, const double *rho_next, int init
         const c64 rn = mk(rho_next[2 * c], rho_next[2 * c + 1]);
         if (init) {
             C.rho = rn;
+            continue;
+        }
+        if (C.restart) { // first iteration of the new seed follows
+            C.beta_prev = mk(0.0, 0.0);
+            C.alpha_prev = mk(1.0, 0.0);
+            C.rho = rn;
+            C.restart = 0;
+            C.iters += 1;
             continue;
         }
         C.beta_prev = cdiv(rn, C.rho);
@@ -366,8 +421,13 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_sI(Panel<T> p) 
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
     cpx<T> a[CPT];
+    unsigned rst = 0; // bit cc: column lane*CPT+cc restarts now (its rt becomes e_j)
 #pragma unroll
-    for (int cc = 0; cc < CPT; ++cc) a[cc] = cvt<T>(p.col[lane * CPT + cc].alpha);
+    for (int cc = 0; cc < CPT; ++cc) {
+        const ColState &C = p.col[lane * CPT + cc];
+        a[cc] = cvt<T>(C.alpha);
+        rst |= (C.restart ? 1u : 0u) << cc;
+    }
     Acc<T> acc[CPT][3];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero(), acc[cc][1].zero(), acc[cc][2].zero();
@@ -381,7 +441,10 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_sI(Panel<T> p) 
             ld_row<T, W>(p.U, row, lane, u);
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
-                rt[cc] = rt[cc] - a[cc] * u[cc];
+                if (rst >> cc & 1u)
+                    rt[cc] = mk<T>(row == p.col[lane * CPT + cc].row ? (T)1 : (T)0, 0);
+                else
+                    rt[cc] = rt[cc] - a[cc] * u[cc];
                 const T rr = rt[cc].re * rt[cc].re, ii = rt[cc].im * rt[cc].im;
                 acc[cc][0].add(rr);
                 acc[cc][0].add(-ii);
@@ -409,7 +472,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_sI(Panel<T> p) 
 
 // -------------------------------------------------------------- kernel B' (S != I)
 template <typename T, int B, int W>
-__global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_update_S(Panel<T> p) {
+__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
     using TM = Teams<T, W, NT>;
     constexpr int CPT = TM::CPT;
     const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
@@ -422,11 +485,14 @@ __global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_update_S(Panel<T> p)
     ld.u = p.U;
     ld.lane = lane;
     cpx<T> a[CPT];
+    unsigned rst = 0; // bit cc: column lane*CPT+cc restarts now (its rt becomes e_j)
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
-        const c64 al = p.col[lane * CPT + cc].alpha;
+        const ColState &C = p.col[lane * CPT + cc];
+        const c64 al = C.alpha;
         a[cc] = cvt<T>(al);
         ld.s[cc] = mk((X)(-al.re), (X)(-al.im));
+        rst |= (C.restart ? 1u : 0u) << cc;
     }
     Acc<T> acc[CPT][2];
 #pragma unroll
@@ -446,7 +512,10 @@ __global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_update_S(Panel<T> p)
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
                 y0[cc] = mk((T)g[cc].re, (T)g[cc].im);
-                rt[cc] = rt[cc] - a[cc] * u[cc];
+                if (rst >> cc & 1u)
+                    rt[cc] = mk<T>(row == p.col[lane * CPT + cc].row ? (T)1 : (T)0, 0);
+                else
+                    rt[cc] = rt[cc] - a[cc] * u[cc];
                 t[cc] = rt[cc] - sy[i][cc];
                 acc[cc][0].add(rt[cc].re * rt[cc].re);
                 acc[cc][0].add(rt[cc].im * rt[cc].im);
@@ -748,7 +817,7 @@ struct SolveLaunch {
     int profile_reps; // > 0: time the kernels of the first panel instead of solving
     double *ms_out;   // [8] average ms per launch (profile)
     Panel<double> pd; // type-erased panel (all T-dependent members are pointers)
-    int ncta_a = 0;   // grid of IC_A, B' and C (0: ncta): they fit one more CTA per SM than A and IC_B
+    int ncta_a = 0;   // grid of IC_A and C (0: ncta): they fit one more CTA per SM than the others
     int rc = TB_OK;
 
     int vec_grid(int W) const {
@@ -774,7 +843,7 @@ struct SolveLaunch {
         k_init_state<T, W><<<1, NT, 0, stream>>>(p, has_s_i);
         k_init_vec<T, W><<<vec_grid(W), NT, 0, stream>>>(p, n_rows, has_s_i);
         if (has_s) {
-            k_update_S<T, B, W><<<grid_a, block, 0, stream>>>(p);
+            k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
             k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
             k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
             k_rho<T, B, W><<<grid_a, block, 0, stream>>>(p, 1);
@@ -791,7 +860,7 @@ struct SolveLaunch {
                 k_outer<T, B, W, false><<<grid, block, 0, stream>>>(p);
             cudaEventRecord(ev[1], stream);
             if (has_s)
-                k_update_S<T, B, W><<<grid_a, block, 0, stream>>>(p);
+                k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
             else
                 k_update_sI<T, B, W><<<grid, block, 0, stream>>>(p);
             cudaEventRecord(ev[2], stream);
@@ -854,7 +923,7 @@ struct SolveLaunch {
         void *a_pinit[] = {&p_init};
         void *a_pinit_rho[] = {&p_init, &init1};
         if (has_s) {
-            last = gb.add_kernel(g, (const void *)k_update_S<T, B, W>, grid_a, block, a_pinit, &last, 1);
+            last = gb.add_kernel(g, (const void *)k_update_S<T, B, W>, grid, block, a_pinit, &last, 1);
             cudaGraph_t ib = nullptr;
             last = gb.add_while(g, h_inner_init, &last, 1, &ib);
             if (!gb.rc) {
@@ -872,7 +941,7 @@ struct SolveLaunch {
             if (has_s) {
                 p_body.h_inner = gb.handle(ob, 0u, 0u);
                 cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, true>, grid, block, a_body, nullptr, 0);
-                x = gb.add_kernel(ob, (const void *)k_update_S<T, B, W>, grid_a, block, a_body, &x, 1);
+                x = gb.add_kernel(ob, (const void *)k_update_S<T, B, W>, grid, block, a_body, &x, 1);
                 cudaGraph_t ib = nullptr;
                 x = gb.add_while(ob, p_body.h_inner, &x, 1, &ib);
                 if (!gb.rc) {

@@ -40,6 +40,11 @@ struct ColState {
     int32_t done, status, iters, n_active, in_done, breakdown;
     int64_t row;    // right-hand side row j (-1: empty slot)
     int64_t dst;    // global column index (-1: empty slot)
+    c64 zs;         // this column's seed shift (changes on a restart)
+    double chk_w;   // worst active shift residual at the last stagnation check
+    int32_t chk_n;  // iteration of that check (-1: none yet)
+    int32_t restarts, restart; // restarts so far; 1 while a restart is in flight
+    int32_t pad_;
 };
 
 struct ShiftState {
@@ -115,6 +120,7 @@ struct Panel {
     cudaGraphConditionalHandle h_outer, h_inner;
     double tol;
     double inner_tol;
+    double stall2;    // seed residual^2 below which a stagnating column restarts (0: never)
     int32_t max_iter;
     int32_t inner_max;
     int32_t outer_cap;
