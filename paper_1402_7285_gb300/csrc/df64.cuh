@@ -82,8 +82,8 @@ __host__ __device__ __forceinline__ df fma(df a, df b, df c) {
 // end.  12 FP32 operations per term instead of 15 for a normalised df fma.
 struct DfSum {
     float s, c;
-    __device__ __forceinline__ void zero() { s = c = 0.f; }
-    __device__ __forceinline__ void add_prod(df a, df b) {
+    __host__ __device__ __forceinline__ void zero() { s = c = 0.f; }
+    __host__ __device__ __forceinline__ void add_prod(df a, df b) {
         const float p = DF_MUL(a.hi, b.hi);
         float e = fmaf(a.hi, b.hi, -p);
         e = fmaf(a.hi, b.lo, e);
@@ -93,7 +93,7 @@ struct DfSum {
         c = DF_ADD(c, DF_ADD(t.lo, e));
     }
     // b exact in FP32 (no low part): 11 operations
-    __device__ __forceinline__ void add_prod(df a, float b) {
+    __host__ __device__ __forceinline__ void add_prod(df a, float b) {
         const float p = DF_MUL(a.hi, b);
         float e = fmaf(a.hi, b, -p);
         e = fmaf(a.lo, b, e);
@@ -103,17 +103,17 @@ struct DfSum {
     }
     // a plain value (a product with 1): the same operations on s and c as
     // add_prod(1, x), without the multiplications
-    __device__ __forceinline__ void add_val(df x) {
+    __host__ __device__ __forceinline__ void add_val(df x) {
         const df t = df_two_sum(s, x.hi);
         s = t.hi;
         c = DF_ADD(c, DF_ADD(t.lo, x.lo));
     }
-    __device__ __forceinline__ void add_val(float x) {
+    __host__ __device__ __forceinline__ void add_val(float x) {
         const df t = df_two_sum(s, x);
         s = t.hi;
         c = DF_ADD(c, t.lo);
     }
-    __device__ __forceinline__ df value() const { return df_fast_two_sum(s, c); }
+    __host__ __device__ __forceinline__ df value() const { return df_fast_two_sum(s, c); }
 };
 
 // a * b and c + a * b for an FP32 operand b (its low part is zero); named, not
