@@ -582,7 +582,6 @@ struct LocalLaunch {
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int g = std::max(1, std::min<int>(grid, sms * std::max(per_sm, 1)));
-        args.scratch = args.scratch; // sized by the caller for `grid` CTAs
         if (has_s)
             k_local<T, B, true><<<g, LNT, sm, stream>>>(a);
         else
