@@ -1,0 +1,58 @@
+"""The roofline accounting of bench.py, recomputed by hand for C2's shapes.
+
+bench.algorithmic_bytes and bench.df_ops turn a kernel's launch time into the
+reported achieved GB/s and FP32-instruction rate; these tests restate the
+per-kernel counts (vectors read and written, matrix once, instruction counts
+per df operation) independently, so a changed formula shows up here."""
+import bench
+
+M, NNZB, B, NBR, W = 131072, 229376, 4, 32768, 32      # C2: SC 32^3, 4 orbitals, panel of 32
+NZ, NENT = 64, 32 * 28                                  # 64 shifts, 28 kept rows per column
+
+
+def test_algorithmic_bytes_df64_panel():
+    V = M * W * 2 * 8               # one complex df panel vector: 67.1 MB
+    Vd = M * W * 2 * 4              # one complex FP32 direction
+    Mb = NNZB * B * B * 8 + NNZB * 4 + (NBR + 1) * 8
+    proj = NENT * NZ * 16
+    got = bench.algorithmic_bytes(M, NNZB, B, NBR, W, NZ, NENT, 8, 4)
+    assert got["A_outer_H_product"] == 9 * V + Mb + 2 * proj     # R, P_old, RT, SP, HP in; P, SP, U, HP out
+    assert got["B_update"] == 6 * V + Mb + 3 * proj
+    assert got["IC_A_inner_S_product"] == 2 * V + 2 * Vd + Mb    # T, D_old in; D, A out
+    assert got["IC_B_inner_update"] == 5 * V + Vd                # Y, D, T, A in; Y, T out
+    assert got["C_rho"] == 2 * V
+    assert abs(V / 1e6 - 67.1) < 0.1 and abs(Mb / 1e6 - 30.5) < 0.1   # 29.4 MB of FP64 values + indices
+
+
+def test_algorithmic_bytes_fp32_panel_has_no_hp():
+    V = M * W * 2 * 4
+    Mb = NNZB * B * B * 4 + NNZB * 4 + (NBR + 1) * 8
+    got = bench.algorithmic_bytes(M, NNZB, B, NBR, W, NZ, NENT, 4, 4)
+    assert got["A_outer_H_product"] == 7 * V + Mb + 2 * NENT * NZ * 16
+
+
+def test_df_ops_ic_a_by_hand():
+    """IC_A per launch: off-diagonal S blocks x FP32 operand (11 instructions per
+    real term), identity diagonal blocks as additions (7), then per own complex
+    element the direction (2 FMAs) and the Hermitian dot d^H a (2 x (6 + 8))."""
+    alg, impl = bench.df_ops(M, NNZB, B, W, s_unit=True)
+    own = M * W
+    prod = (NNZB - NBR) * B * B * 2 * W * 11 + NBR * B * 2 * W * 7
+    assert alg["IC_A_inner_S_product"] == prod + own * (2 + 2 * (6 + 8))
+    # implemented: each neighbour's direction value is formed again per referencing block
+    assert impl["IC_A_inner_S_product"] - alg["IC_A_inner_S_product"] == NNZB * B * W * 2
+
+
+def test_df_ops_outer_and_streaming_kernels_by_hand():
+    alg, impl = bench.df_ops(M, NNZB, B, W, s_unit=True)
+    own = M * W
+    cx_axpy = 4 * 7 + 4 * 11
+    dot = 4 * (7 + 8)
+    assert alg["A_outer_H_product"] == NNZB * B * B * 2 * W * 12 + own * (4 * cx_axpy + dot)
+    assert alg["IC_B_inner_update"] == own * (2 * 14 + 2 * 15 + 2 * (7 + 8))
+    assert alg["C_rho"] == own * dot
+    assert impl["A_outer_H_product"] == alg["A_outer_H_product"]        # H r: no operand formed on the fly
+
+
+def test_fp32_peak_is_the_lane_count_times_the_clock():
+    assert bench.FP32_PEAK_OPS == 152 * 128 * 2.07e9
