@@ -211,6 +211,9 @@ void tb_solve_opts_default(tb_solve_opts *opts);
  * every diagonal block of S is the identity (orthonormal orbitals on each
  * site; checked on the device per call) the S products add those blocks'
  * operand instead of multiplying by them, with the same result bits.
+ * TB_PREC_DF64: a column whose hardest unconverged shift stops improving while
+ * the seed residual is below 1e-10 restarts with that shift as its seed
+ * (converged shifts keep their results; iters counts every iteration run).
  * Returns TB_OK, or a positive OR of TB_WARN_* when some column did not
  * converge, or a negative error. */
 int shifted_cocg_solve(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z,
