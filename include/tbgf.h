@@ -204,16 +204,24 @@ void tb_solve_opts_default(tb_solve_opts *opts);
  * Outputs: G complex [out_row_ptr[n_rhs]][n_z]; iters int32[n_rhs] (outer
  * iterations run); resid double[n_rhs][n_z] (final recurrence residual
  * ||rt_n|| / |pi^m_n| relative to ||b||); status int32[n_rhs] (TB_COL_*).
- * Method: one seed COCG per column in the S-bilinear form with the shifted
- * systems following through collinear residuals (Sec. 3; recurrences in the
- * library's design notes), columns batched into panels so that one block
+ * Method: one seed COCG per column in the S-bilinear form <u,v> = u^T S v
+ * (Sec. 3's generalized shifted COCG): p = r + beta p, u = (z_s S - H) p,
+ * alpha = r^T S r / p^T u, S r <- S r - alpha u, r = S^-1 (S r) by an inner CG;
+ * every shift z_m follows through collinear residuals r_m = r / pi_m, with
+ * pi_{n+1} = (1 + alpha_n (z_m - z_s)) pi_n + (alpha_n beta_{n-1} /
+ * alpha_{n-1}) (pi_n - pi_{n-1}) and x_m += (alpha_n pi_n / pi_{n+1}) p_m
+ * kept on the requested rows only; columns batched into panels so that one block
  * sparse product per iteration serves every column and every shift.  When
  * every diagonal block of S is the identity (orthonormal orbitals on each
  * site; checked on the device per call) the S products add those blocks'
  * operand instead of multiplying by them, with the same result bits.
- * TB_PREC_DF64: a column whose hardest unconverged shift stops improving while
- * the seed residual is below 1e-10 restarts with that shift as its seed
- * (converged shifts keep their results; iters counts every iteration run).
+ * TB_PREC_DF64 restart: once a column's seed residual ||S r|| is below 1e-10,
+ * its worst unconverged shift residual is checked every 512 outer
+ * iterations; if it fell by less than 1 % since the previous check, the
+ * column restarts with that shift as its new seed: converged shifts keep
+ * their results, every unconverged shift starts again from x = 0, and the
+ * restart itself takes one outer iteration.  At most two restarts per
+ * column; iters counts every iteration run, before and after restarts.
  * Returns TB_OK, or a positive OR of TB_WARN_* when some column did not
  * converge, or a negative error. */
 int shifted_cocg_solve(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z,
@@ -325,19 +333,24 @@ int gf_reduce_ldos_dm(tb_ctx *ctx, const double *G, int32_t n_z, const double *z
  * synchronisation of cudaFree, an embedding host forbids allocation after
  * start-up).  Same result as gf_reduce_ldos_dm, but it calls no cudaMalloc,
  * cudaFree or allocating routine: its scratch (one weight per kept entry and
- * a flag) is a static device array of TB_REDUCE_STATIC_MAX_ENTRIES + 32
- * doubles that every GPU loading the library holds until exit.
- *  - n_out must equal out_row_ptr[n_rhs] and be <= TB_REDUCE_STATIC_MAX_ENTRIES
+ * four check flags) is a static device array of TB_REDUCE_STATIC_MAX_ENTRIES
+ * + 32 doubles that every GPU loading the library holds until exit.
+ *  - n_out (the number of kept entries) must be <= TB_REDUCE_STATIC_MAX_ENTRIES
  *    (else TB_ERR_SIZE, nothing queued);
  *  - every array (G, z, w, rhs_rows, out_row_ptr, out_rows, S's arrays, ldos,
- *    dm) must be device memory of the current device (else TB_ERR_ARG);
+ *    dm) must be device (or managed) memory of the current device (else
+ *    TB_ERR_ARG);
+ *  - each call first checks its index arrays on the device and synchronises
+ *    the stream once to read the result; nothing is written to ldos or dm
+ *    unless out_row_ptr starts at 0, is monotone and ends at n_out (else
+ *    TB_ERR_SIZE), every row and rhs row lies inside S (else TB_ERR_ARG), S's
+ *    structure is well formed (else TB_ERR_STRUCTURE) and, with S = NULL and
+ *    ldos requested, every column keeps its own row (else TB_ERR_ARG);
  *  - the first call on a device looks up the scratch address
  *    (cudaGetSymbolAddress) with that device current; make it before any
  *    stream capture;
  *  - all calls share the scratch: calls whose GPU work overlaps (other
- *    streams or host threads) race; calls on one stream are ordered;
- *  - with S = NULL the call synchronises the stream once to check that each
- *    column keeps its own row. */
+ *    streams or host threads) race; calls on one stream are ordered. */
 #define TB_REDUCE_STATIC_MAX_ENTRIES 524288
 int gf_reduce_ldos_dm_static(tb_ctx *ctx, const double *G, int32_t n_z, const double *z, const double *w,
                              double mu, double kT, const int64_t *rhs_rows, int64_t n_rhs,

@@ -144,6 +144,10 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Checks a device BSR structure (row_ptr monotone from 0 to nnzb, col_idx in
 // range and ascending within each block row) and the 16-byte alignment of its
 // values; returns TB_OK or TB_ERR_STRUCTURE / TB_ERR_ARG.  Synchronises `s`.
+// Structure check of validate_bsr as a kernel: ORs 1 into *bad for a bad
+// row pointer, 2 for a column index out of range or out of order.
+__global__ void k_validate_bsr(const int64_t *rp, const int32_t *ci, int64_t n_brows, int64_t nnzb, int *bad);
+
 int validate_bsr(tb_ctx *ctx, const int64_t *row_ptr, const int32_t *col_idx, const void *val, int64_t n_brows,
                  int64_t nnzb, cudaStream_t s, const char *name);
 
