@@ -148,24 +148,36 @@ def kernel_traffic(kernel: str, precision: str = "df64", W: int = 32) -> int | N
     return int(m.group(1)) if m else None
 
 
-def algorithmic_bytes(n_rows, nnzb, bdim, n_brows, W, n_z, n_ent, esz, dsz):
+def algorithmic_bytes(n_rows, nnzb, bdim, n_brows, W, n_z, n_ent, esz, dsz, refine=False):
     """Bytes each solver kernel must move once per launch (matrix read once, panel vectors once).
 
     esz: bytes per real of the panel vectors; dsz: of the inner CG's direction
     vectors (FP32 with df panels).  FP64 and df panels keep H p by recurrence
-    (read and written by A); FP32 panels do not."""
+    (read and written by A); FP32 panels do not.  refine: the df inner solve by
+    refinement, whose FP32 sweeps (IC_A, IC_B) work on FP32 vectors with FP32
+    values of S, and whose refinement pass R updates the df solution and
+    residual with a df product of S."""
     hp = 2 if esz == 8 else 0
     V = n_rows * W * 2 * esz                     # one complex panel vector
     Vd = n_rows * W * 2 * dsz                    # one inner CG direction vector
-    Mb = nnzb * bdim * bdim * esz + nnzb * 4 + (n_brows + 1) * 8
+    V32 = n_rows * W * 2 * 4                     # one FP32 complex panel vector
+    idx = nnzb * 4 + (n_brows + 1) * 8
+    Mb = nnzb * bdim * bdim * esz + idx
+    Mb32 = nnzb * bdim * bdim * 4 + idx
     proj = n_ent * n_z * 16                      # one FP64 complex projected-state array
-    return {
+    out = {
         "A_outer_H_product": (7 + hp) * V + Mb + 2 * proj,  # R, P_old, RT, SP, HP in; P, SP, U, HP out; p^m rw
         "B_update": 6 * V + Mb + 3 * proj,              # RT, U, R in; RT, R', T out; S; x^m rw, p^m in
         "IC_A_inner_S_product": 2 * V + 2 * Vd + Mb,    # T, D_old in; D, A out; S
         "IC_B_inner_update": 5 * V + Vd,                # Y, D, T, A in; Y, T out
         "C_rho": 2 * V,                                 # R, RT in
     }
+    if refine:
+        out["B_update"] += V32                          # + the first sweep's FP32 residual
+        out["IC_A_inner_S_product"] = 4 * V32 + Mb32    # T32, D_old in; D, A32 out; FP32 S
+        out["IC_B_inner_update"] = 6 * V32              # C32, T32 rw; D, A32 in
+        out["R_refine"] = 4 * V + 2 * V32 + Mb          # Y, T rw (df); C32 in, T32 out; df S
+    return out
 
 
 # FP32 instructions per df operation as implemented (csrc/df64.cuh): a lazily
@@ -201,6 +213,7 @@ def df_ops(n_rows, nnzb, bdim, W, s_unit=True):
         "IC_B_inner_update": own * (2 * DF_FMA_F + 2 * DF_FMA + norm),
         "C_rho": own * dot,
     }
+    alg["R_refine"] = prod_s + own * (2 * (DF_ADD + 1) + 2 * DF_ADD + norm)   # S c; y += c, t -= S c; ||t||^2
     extra = {"B_update": nb * 4, "IC_A_inner_S_product": nb * 2}
     impl = {k: v + extra.get(k, 0) for k, v in alg.items()}
     return alg, impl
@@ -234,6 +247,60 @@ def unit_diagonal(S) -> bool:
     rows = np.repeat(np.arange(S.n_brows), np.diff(rp))
     diag = val[ci == rows]
     return diag.shape[0] == S.n_brows and bool(np.all(diag == np.eye(S.bdim)))
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_panel0_goldens.npz")
+
+
+def rel_errors(G, L, D, ptr, ref_G, ref_L, ref_D, ref_ptr):
+    """Per-output relative errors of the solver's G, LDOS and DM against reference values.
+
+    G: per (column, shift) the largest |dG| over the kept rows relative to the
+    largest |G_ref| of that column and shift; LDOS: per (column, shift) |dL| / |L_ref|;
+    DM: per column the largest |dD| relative to the largest |D_ref| of that column."""
+    eg, el, ed = [], [], []
+    for c in range(len(ref_ptr) - 1):
+        g, gr = G[ptr[c]:ptr[c + 1]], ref_G[ref_ptr[c]:ref_ptr[c + 1]]
+        eg.append(np.abs(g - gr).max(axis=0) / np.abs(gr).max(axis=0))
+        el.append(np.abs(L[c] - ref_L[c]) / np.abs(ref_L[c]))
+        d, dr = D[ptr[c]:ptr[c + 1]], ref_D[ref_ptr[c]:ref_ptr[c + 1]]
+        ed.append(np.abs(d - dr).max() / np.abs(dr).max())
+    eg, el, ed = np.concatenate(eg), np.concatenate(el), np.asarray(ed)
+    return {"G": {"max": float(eg.max()), "median": float(np.median(eg))},
+            "LDOS": {"max": float(el.max()), "median": float(np.median(el))},
+            "DM": {"max": float(ed.max()), "median": float(np.median(ed))}}
+
+
+def golden_accuracy(res, panel_dev):
+    """Errors of the first timed panel's outputs on the columns the stored oracle results cover.
+
+    The stored results (tests/golden/c2_panel0_goldens.npz, written by the oracle
+    alone) hold four columns of panel 0: the oracle's plain FP64 shifted COCG at
+    this tolerance (1e-5) and at 1e-9 (close to the exact Green's function)."""
+    if not os.path.exists(GOLDEN):
+        return {"unavailable": "tests/golden/c2_panel0_goldens.npz is missing"}
+    g = np.load(GOLDEN)
+    cols, ptr, orows = (a.cpu().numpy() for a in panel_dev)
+    slots = g["slots"]
+    if not np.array_equal(cols[slots], g["cols"]):
+        return {"unavailable": "the first timed panel does not hold the stored columns"}
+    G = res.G.cpu().numpy()
+    L = res.ldos.cpu().numpy()
+    D = res.dm.cpu().numpy()
+    sel_G, sel_D, sel_ptr = [], [], [0]
+    for c in slots:
+        sel_G.append(G[ptr[c]:ptr[c + 1]])
+        sel_D.append(D[ptr[c]:ptr[c + 1]])
+        assert np.array_equal(orows[ptr[c]:ptr[c + 1]], g["out_rows"][g["out_ptr"][len(sel_ptr) - 1]:
+                                                                     g["out_ptr"][len(sel_ptr)]])
+        sel_ptr.append(sel_ptr[-1] + ptr[c + 1] - ptr[c])
+    Gs, Ds, Ls = np.concatenate(sel_G), np.concatenate(sel_D), L[slots]
+    out = {"columns": [int(x) for x in g["cols"]], "definition": rel_errors.__doc__.split("\n\n")[1].strip()}
+    for tag, name in (("tol5", "vs_fp64_oracle_same_tol"), ("tol9", "vs_fp64_oracle_tol_1e-9")):
+        out[name] = rel_errors(Gs, Ls, Ds, sel_ptr, g[f"G_{tag}"], g[f"ldos_{tag}"], g[f"dm_{tag}"], g["out_ptr"])
+    out["oracle_fp64_same_tol_vs_tol_1e-9"] = rel_errors(g["G_tol5"], g["ldos_tol5"], g["dm_tol5"], g["out_ptr"],
+                                                         g["G_tol9"], g["ldos_tol9"], g["dm_tol9"], g["out_ptr"])
+    return out
 
 
 def run_ours(args, rank, world):
@@ -282,6 +349,7 @@ def run_ours(args, rank, world):
         r = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=prec, panel_w=W,
                      max_iter=args.max_iter, ctas_per_sm=args.ctas_per_sm)
         L, D = tb.reduce_ldos_dm(ctx, r.G, zt, wt, mu, kT, cols, ptr, orows, S=S)
+        r.ldos, r.dm = L, D
         return r
 
     def converged_pairs(r):
@@ -292,8 +360,11 @@ def run_ours(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
 
-    panels = [dev_panel(s) for s in range(args.warmup + args.steps)]
-    for s in range(args.warmup):
+    # timed steps take panels 0, 1, ... (so the first timed panel is always panel 0,
+    # whose columns the stored oracle results cover); warm-up steps take the panels after them
+    order = list(range(args.steps + args.warmup))
+    panels = [dev_panel(s) for s in order]
+    for s in range(args.steps, args.steps + args.warmup):
         step_device(*panels[s])
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -303,7 +374,7 @@ def run_ours(args, rank, world):
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        for s in range(args.warmup, args.warmup + args.steps):
+        for s in range(args.steps):
             results.append(step_device(*panels[s]))
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -312,7 +383,12 @@ def run_ours(args, rank, world):
     pairs = sum(converged_pairs(r) for r in results)
     outer = sum(r.outer_iters for r in results)
     inner = sum(r.inner_iters for r in results)
-    launches = sum(13 + 3 * r.outer_iters + 2 * r.inner_iters for r in results)
+    refines = sum(r.refinements for r in results)
+    # per panel: 13 set-up and write-out launches, A, B and C per outer iteration,
+    # IC_A and IC_B per inner step and (df64 refinement) one R per inner step
+    refine_mode = prec == tb.TB_PREC_DF64
+    launches = sum(13 + 3 * r.outer_iters + (3 if refine_mode else 2) * r.inner_iters for r in results)
+    accuracy = golden_accuracy(results[0], panels[0]) if rank == 0 else None
     ms_max, pairs_all, launches_all = sharding.reduce_step_stats(ms, float(pairs), float(launches), world, dev)
     value = pairs_all / (ms_max / 1e3)
 
@@ -325,7 +401,7 @@ def run_ours(args, rank, world):
         zp = pin(z)
         wp = pin(w_q)
         e2e_steps = max(1, min(args.steps, args.e2e_steps))
-        host_panels = [tuple(pin(a) for a in panel(args.warmup + s)) for s in range(e2e_steps)]
+        host_panels = [tuple(pin(a) for a in panel(order[s])) for s in range(e2e_steps)]
         h2d = sum(int(a.numel() * a.element_size()) for a in (Hp.row_ptr, Hp.col_idx, Hp.val, Sp.row_ptr,
                                                              Sp.col_idx, Sp.val, zp, wp))
         barrier()
@@ -349,7 +425,7 @@ def run_ours(args, rank, world):
     # ---- the plain FP64 solver on the same panel (the comparison the metric names)
     fp64 = None
     if args.fp64_compare and prec != tb.TB_PREC_FP64:
-        cols, ptr, orows = panels[args.warmup]
+        cols, ptr, orows = panels[0]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -369,37 +445,39 @@ def run_ours(args, rank, world):
     prof = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W,
                       ctas_per_sm=args.ctas_per_sm)
     counts = {"A_outer_H_product": outer, "B_update": outer, "IC_A_inner_S_product": inner,
-              "IC_B_inner_update": inner, "C_rho": outer}
-    share = {k: prof[k] * counts[k] for k in prof}
+              "IC_B_inner_update": inner, "C_rho": outer, "R_refine": refines}
+    share = {k: prof[k] * counts[k] for k in prof if prof[k] > 0}
     dom = max(share, key=share.get)
     n_ent = int(ptr[-1].item())
     esz = 4 if prec == tb.TB_PREC_MIXED else 8      # bytes per real: FP32, or FP64 / df pairs
     dsz = 4 if prec != tb.TB_PREC_FP64 else 8       # inner CG directions: FP32 with df panels
-    algo = algorithmic_bytes(Hh.n_rows, Hh.nnzb, Hh.bdim, Hh.n_brows, W, n_z, n_ent, esz, dsz)
+    algo = algorithmic_bytes(Hh.n_rows, Hh.nnzb, Hh.bdim, Hh.n_brows, W, n_z, n_ent, esz, dsz, refine=refine_mode)
     peaks = measured_peaks()
     achieved = algo[dom] / (prof[dom] * 1e-3) / 1e9
-    hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-           "peak_source": peaks["source"] + " (burst, kernel timed alone)", "bytes_per_launch": algo[dom]}
-    if prec == tb.TB_PREC_DF64:
-        # double-float products are bound by the FP32 pipes (ncu: FMA pipe ~50-60% active), not by HBM
+    # the metric's roofline: algorithmic bytes of the dominant kernel per launch / its
+    # CUDA-event time, against the measured HBM copy peak
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"] + " (burst, kernel timed alone)",
+            "bytes_per_launch": algo[dom], "traffic": kernel_traffic(dom, args.precision, W)}
+    if prec == tb.TB_PREC_DF64 and dom in ("A_outer_H_product", "B_update", "C_rho", "R_refine"):
+        # double-float kernels are limited by FP32 instruction issue: the same launch
+        # measured in FP32 instructions of its df arithmetic (secondary figure)
         ops, ops_impl = df_ops(Hh.n_rows, Hh.nnzb, Hh.bdim, W, s_unit=unit_diagonal(Sh))
         ach = ops[dom] / (prof[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_OPS / 1e12,
-                "unit": "TFLOP/s", "frac": ach / (FP32_PEAK_OPS / 1e12),
-                "op_definition": "FP32 instructions of the df arithmetic with every vector element formed once "
-                                 "(one per lane per clock); peak = 152 SMs x 128 FP32 lanes x 2.07 GHz",
-                "ops_per_launch": ops[dom], "ops_per_launch_implemented": ops_impl[dom],
-                "traffic": kernel_traffic(dom, args.precision, W), "hbm": hbm}
-    else:
-        roof = {"bound": "alu" if prec == tb.TB_PREC_FP64 else "hbm", "kernel": dom, **hbm,
-                "traffic": kernel_traffic(dom, args.precision, W)}
+        roof["alu"] = {"achieved": ach, "peak": FP32_PEAK_OPS / 1e12, "unit": "T FP32 instr/s",
+                       "frac": ach / (FP32_PEAK_OPS / 1e12), "ops_per_launch": ops[dom],
+                       "ops_per_launch_implemented": ops_impl[dom],
+                       "op_definition": "FP32 instructions of the df arithmetic with every vector element formed "
+                                        "once; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz"}
     roof.update({"ms_per_launch": prof[dom], "per_kernel_ms": prof,
+                 "per_kernel_launches": counts,
                  "per_kernel_share": {k: share[k] / sum(share.values()) for k in share},
                  "per_kernel_gbs": {k: algo[k] / (prof[k] * 1e-3) / 1e9 for k in prof if prof[k] > 0}})
     spmm = spmm_bandwidth(tb, ctx, H, Hh, peaks) if rank == 0 else None
     ctx.close()
     return {"value": value, "ms": ms_max, "pairs": pairs_all, "launches": launches_all, "clocks": clk.summary(),
             "e2e": e2e, "roofline": roof, "spmm": spmm, "outer_iters": outer, "inner_iters": inner, "fp64": fp64,
+            "refinements": refines, "accuracy": accuracy,
             "iters_per_column": [int(x) for r in results for x in (r.iters.cpu().numpy() if hasattr(r.iters, "cpu")
                                                                     else r.iters)]}
 
@@ -642,7 +720,9 @@ def main():
             "clocks": out["clocks"], "e2e": out["e2e"], "gpu_launches": int(out["launches"]),
             "roofline": out["roofline"], "spmm_hbm": out["spmm"], "cpu_baseline": cpu,
             "solver": {"outer_iters": out["outer_iters"], "inner_iters": out["inner_iters"],
+                       "refinements": out["refinements"],
                        "mean_iters_per_column": float(np.mean(out["iters_per_column"]))},
+            "accuracy": out["accuracy"],
             "plain_fp64": out["fp64"]}
     print(json.dumps(line))
     if world > 1:

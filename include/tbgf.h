@@ -141,10 +141,13 @@ int tb_build_csr(const tb_system_spec *spec, uint64_t seed, tb_bsr *H, tb_bsr *S
                            tests, projected solutions and reductions           */
 #define TB_PREC_DF64 2  /* vectors, SpMM and updates in double-float (hi + lo
                            FP32 pairs, ~48 bits) on the FP32 pipes; FP64
-                           scalars, projections and reductions as above; the
-                           inner CG's search directions and starting guess
-                           (which steer it but do not enter its result) in
-                           FP32                                                */
+                           scalars, projections and reductions as above.  With
+                           S, the inner solve S r = rt is iterative refinement:
+                           the residual t = rt - S y is kept in df, FP32 CG
+                           sweeps solve S c = t (FP32 vectors, FP32 values of S,
+                           two-float dot products) and each sweep's c is added
+                           to y in df, t -= S c with a df product, until
+                           ||t|| <= inner_tol ||rt||                            */
 
 /* Y = A X for a real BSR matrix A (n = n_brows*bdim rows) and a complex panel
  * X of ncols columns: X, Y complex double [n][ncols] (row-major, interleaved).
@@ -178,16 +181,18 @@ typedef struct {
                             and keeps the fastest per column (cached per shape
                             in the context); fewer columns use a heuristic     */
     int32_t seed_shift;  /* index of the seed shift; -1 = median Re z (default)    */
-    double inner_tol;    /* S != I: relative tolerance of the inner CG on S; 0 =
-                            max(1e-3 tol, floor), floor 1e-13 FP64, 1e-12 DF64,
-                            1e-7 mixed                                            */
-    int32_t inner_max;   /* S != I: inner iterations per outer iteration, 0 = 40   */
+    double inner_tol;    /* S != I: relative tolerance ||S r - rt|| <= inner_tol ||rt||
+                            of the inner solve on S; 0 = max(1e-3 tol, 1e-13) FP64,
+                            max(1e-3 tol, 1e-7) mixed, max(1e-5 tol, 1e-12) DF64   */
+    int32_t inner_max;   /* S != I: inner iterations per outer iteration (DF64: per
+                            FP32 sweep), 0 = 40                                   */
     int32_t ctas_per_sm; /* resident CTAs per SM for the panel kernels, 0 = 3;
                             with df panels and block edges <= 4 the inner S
                             product and the rho kernel run one more (at most 4) */
     void *stream;        /* cudaStream_t to queue work on                         */
-    int64_t *stats;      /* optional host array [2]: outer and inner iterations
-                            summed over all panels (written before returning)     */
+    int64_t *stats;      /* optional host array [3]: outer iterations, inner
+                            iterations and (DF64 with S) refinement passes summed
+                            over all panels (written before returning)            */
 } tb_solve_opts;
 
 /* Fill `opts` with the defaults above. */

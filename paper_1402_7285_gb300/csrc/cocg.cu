@@ -87,7 +87,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
              TB_ERR_ARG, "panel_w must be 0, 8, 16, 32 or 64");
     TB_CHECK(ctx, opts.seed_shift >= -1 && opts.seed_shift < n_z, TB_ERR_ARG, "seed_shift out of range");
     TB_CHECK(ctx, !profiling || (ms && n_rhs > 0), TB_ERR_ARG, "profile needs right-hand sides and ms[]");
-    if (opts.stats) opts.stats[0] = opts.stats[1] = 0;
+    if (opts.stats) opts.stats[0] = opts.stats[1] = opts.stats[2] = 0;
     if (n_rhs == 0) return TB_OK;
     cudaStream_t stream = (cudaStream_t)opts.stream;
     const bool mixed = opts.precision == TB_PREC_MIXED;
@@ -190,6 +190,10 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const size_t esz = mixed ? 4 : 8;
     const size_t vec_bytes = align_up(esz * 2 * n_rows * W, 256);
     const int n_vec = (has_s ? 11 : 4) + (mixed ? 0 : 1); // + H p (recurrence) unless FP32
+    // df panels with S: the inner solve runs as FP32 sweeps with df refinement
+    // (FP32 sweep residual, correction and product: three FP32 vectors)
+    const bool ir = has_s && opts.precision == TB_PREC_DF64;
+    const size_t vec32_bytes = align_up(sizeof(float) * 2 * n_rows * W, 256);
     const int per_cta = NT / (W / (mixed ? 2 : 1));
     TB_CHECK(ctx, opts.ctas_per_sm >= 0 && opts.ctas_per_sm <= 8, TB_ERR_ARG, "ctas_per_sm must be 0..8");
     const int per_sm = opts.ctas_per_sm > 0 ? opts.ctas_per_sm : 3;
@@ -198,12 +202,16 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     // IC_A and C are compiled for four resident CTAs per SM (df panels, block edges <= 4): one more
     // than the other kernels
     int ncta_a = ncta;
+    // the FP32 sweep kernels of the refinement: FP32 team geometry (two complex per thread)
+    const int per_cta_f = NT / (W / 2);
+    const int ncta_f = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * num_sms(),
+                                                                   (H->n_brows + per_cta_f - 1) / per_cta_f));
     if (b <= 4 && opts.precision == TB_PREC_DF64 && per_sm < 4)
         ncta_a = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(per_sm + 1) * num_sms(),
                                                              (H->n_brows + per_cta - 1) / per_cta));
-    const int ncta_max = std::max(ncta, ncta_a);
+    const int ncta_max = std::max(std::max(ncta, ncta_a), ncta_f);
     void *vec_base = nullptr;
-    rc = ws_get(ctx, WS_SOLVE_VEC, vec_bytes * n_vec, &vec_base);
+    rc = ws_get(ctx, WS_SOLVE_VEC, vec_bytes * n_vec + (ir ? 3 * vec32_bytes : 0), &vec_base);
     if (rc) return rc;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -222,10 +230,11 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const size_t o_pebase = take(sizeof(int64_t) * pan_ebase.size());
     const size_t o_erow = take(sizeof(int64_t) * std::max<int64_t>(n_out, 1));
     const size_t o_edst = take(sizeof(int64_t) * ent_dst.size());
-    const size_t o_stats = take(sizeof(int64_t) * 2 * n_panels);
+    const size_t o_stats = take(sizeof(int64_t) * 3 * n_panels);
     const size_t vsz = mixed ? sizeof(float) : sizeof(double);
     const size_t o_h32 = lowp ? take(vsz * H->nnzb * bb) : 0;
     const size_t o_s32 = (lowp && has_s) ? take(vsz * S->nnzb * bb) : 0;
+    const size_t o_sf32 = ir ? take(sizeof(float) * S->nnzb * bb) : 0; // FP32 S for the sweeps
     void *small_base = nullptr;
     rc = ws_get(ctx, WS_SOLVE_SMALL, off, &small_base);
     if (rc) return rc;
@@ -235,7 +244,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     if (rc) return rc;
 
     TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_ctl, 0, sizeof(Ctrl), stream));
-    TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_stats, 0, sizeof(int64_t) * 2 * n_panels, stream));
+    TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_stats, 0, sizeof(int64_t) * 3 * n_panels, stream));
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_prow, pan_row.data(), sizeof(int64_t) * pan_row.size(), cudaMemcpyHostToDevice, stream));
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_pdst, pan_dst.data(), sizeof(int64_t) * pan_dst.size(), cudaMemcpyHostToDevice, stream));
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_peptr, pan_eptr.data(), sizeof(int32_t) * pan_eptr.size(), cudaMemcpyHostToDevice, stream));
@@ -251,6 +260,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
         if (has_s) {
             convert_values(opts.precision, (const double *)d_sval, sb + o_s32, S->nnzb * bb, stream);
             sval = sb + o_s32;
+            if (ir) convert_values(TB_PREC_MIXED, (const double *)d_sval, sb + o_sf32, S->nnzb * bb, stream);
         }
     }
     TB_CUDA_TRY(ctx, cudaGetLastError());
@@ -284,6 +294,14 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
         p.D[1] = vec();
         p.Av = vec();
     }
+    if (ir) {
+        char *v32 = vb + vec_bytes * vi;
+        p.T32 = (float *)v32;
+        p.C32 = (float *)(v32 + vec32_bytes);
+        p.A32 = (float *)(v32 + 2 * vec32_bytes);
+        p.s_val32 = (const float *)(sb + o_sf32);
+        p.ir = 1;
+    }
     p.col = (ColState *)(sb + o_col);
     p.sh = (ShiftState *)(sb + o_sh);
     p.nz = n_z;
@@ -304,7 +322,14 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.ctl = (Ctrl *)(sb + o_ctl);
     p.tol = opts.tol;
     p.stall2 = opts.precision == TB_PREC_DF64 ? 1e-20 : 0.0; // df64 restarts (see k_outer)
-    p.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol : std::max(1e-3 * opts.tol, mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13));
+    // inner tolerance: FP64 and FP32 panels 1e-3 tol (floors 1e-13, 1e-7); df panels
+    // refine to 1e-5 tol (floor 1e-12): the refinement makes the tighter target cheap,
+    // and inexact inner solves are what separates the shifted results from the FP64 ones
+    p.inner_tol = opts.inner_tol > 0.0 ? opts.inner_tol
+                                       : (ir ? std::max(1e-5 * opts.tol, 1e-12)
+                                             : std::max(1e-3 * opts.tol, mixed ? 1e-7 : (lowp ? 1e-12 : 1e-13)));
+    p.refine_max = 8;
+    p.sweep_red = 1e-5;
     p.max_iter = opts.max_iter;
     p.inner_max = opts.inner_max > 0 ? opts.inner_max : 40;
     p.outer_cap = opts.max_iter + 2;
@@ -317,6 +342,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     SolveLaunch L{ctx, has_s, ncta, n_rows, n_panels, stream, profile_reps, ms};
     L.pd = p;
     L.ncta_a = ncta_a;
+    L.ncta_f = ncta_f;
     const bool launched = opts.precision == TB_PREC_FP64    ? launch_panel_f64(L, b, W)
                           : opts.precision == TB_PREC_MIXED ? launch_panel_f32(L, b, W)
                                                             : launch_panel_df(L, b, W);
@@ -325,11 +351,12 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     TB_CUDA_TRY(ctx, cudaGetLastError());
     if (profiling) return TB_OK;
     if (opts.stats) {
-        std::vector<int64_t> st2(2 * (size_t)n_panels);
-        TB_CUDA_TRY(ctx, cudaMemcpy(st2.data(), sb + o_stats, sizeof(int64_t) * st2.size(), cudaMemcpyDeviceToHost));
+        std::vector<int64_t> st3(3 * (size_t)n_panels);
+        TB_CUDA_TRY(ctx, cudaMemcpy(st3.data(), sb + o_stats, sizeof(int64_t) * st3.size(), cudaMemcpyDeviceToHost));
         for (int i = 0; i < n_panels; ++i) {
-            opts.stats[0] += st2[2 * i];
-            opts.stats[1] += st2[2 * i + 1];
+            opts.stats[0] += st3[3 * i];
+            opts.stats[1] += st3[3 * i + 1];
+            opts.stats[2] += st3[3 * i + 2];
         }
     }
     std::vector<int32_t> stv(n_rhs);

@@ -59,6 +59,8 @@ __global__ void k_init_state(Panel<T> p, int has_s) {
         p.ctl->iter_ctr = 0;
         p.ctl->in_ctr = 0;
         p.ctl->inner_total = 0;
+        p.ctl->refine_total = 0;
+        p.ctl->refine_now = 0;
     }
 }
 
@@ -305,7 +307,9 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
         const c64 mu = mk(red[2 * c], red[2 * c + 1]);
         const int n_active = atomicAdd(&C.n_active, 0);
         int st = -1;
-        if (n_active <= 0)
+        if (C.s_bad)
+            st = TB_COL_BREAKDOWN; // S is not positive definite on an inner CG direction
+        else if (n_active <= 0)
             st = C.breakdown ? TB_COL_BREAKDOWN : TB_COL_CONVERGED;
         else if (!cfinite(mu) || !cfinite(C.rho))
             st = TB_COL_NONFINITE;
@@ -486,6 +490,10 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
     ld.lane = lane;
     cpx<T> a[CPT];
     unsigned rst = 0; // bit cc: column lane*CPT+cc restarts now (its rt becomes e_j)
+    // refinement: the first FP32 sweep sees t_0 / ||rt_n|| (no FP32 underflow however
+    // small the residuals of a tight solve become); a restarting column's residual
+    // becomes e_j, of norm one, so its scale is one
+    float inv_sig = 1.f;
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) {
         const ColState &C = p.col[lane * CPT + cc];
@@ -493,6 +501,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
         a[cc] = cvt<T>(al);
         ld.s[cc] = mk((X)(-al.re), (X)(-al.im));
         rst |= (C.restart ? 1u : 0u) << cc;
+        if (cc == 0) inv_sig = (float)(1.0 / (C.restart ? 1.0 : safe_scale(C.rn2)));
     }
     Acc<T> acc[CPT][2];
 #pragma unroll
@@ -525,6 +534,12 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
             st_row<T, W>(p.RT, row, lane, rt);
             st_row<T, W>(Rn, row, lane, y0);
             st_row<T, W>(p.Tv, row, lane, t);
+            if constexpr (std::is_same<T, df>::value) {
+                if (p.ir) { // the first FP32 sweep solves S c' = t_0 / ||rt_n||
+                    const int64_t o = (row * W + lane) * 2;
+                    *reinterpret_cast<float2 *>(p.T32 + o) = make_float2(t[0].re.hi * inv_sig, t[0].im.hi * inv_sig);
+                }
+            }
         }
     }
     cta_partials<T, W, NT, 2>(acc, p.part);
@@ -541,18 +556,36 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
         C.in_beta = 0.0;
         if (C.done) {
             C.in_done = 1;
+            C.in_sweep = 0;
             continue;
         }
+        const double sig = C.restart ? 1.0 : safe_scale(C.rn2); // the scale the rows used
         C.rn2 = red[2 * c];
         C.in_rr = red[2 * c + 1];
-        C.in_tol2 = p.inner_tol * p.inner_tol * C.rn2;
-        C.in_done = (C.in_rr <= C.in_tol2) ? 1 : 0;
+        if (p.ir) {
+            // refinement: the column sweeps until its true residual t = rt - S y is
+            // below inner_tol ||rt||; each FP32 sweep works on t / in_sig and
+            // reduces its own residual by sweep_red (or to half the final target)
+            const double eta2 = p.inner_tol * p.inner_tol * C.rn2;
+            C.in_t2 = C.in_rr;
+            C.in_sig = sig;
+            C.in_rr = C.in_t2 / (sig * sig);
+            C.in_refines = 0;
+            C.in_conv = !(C.in_t2 > eta2) || !isfinite(C.in_t2);
+            C.in_sweep = !C.in_conv;
+            C.in_done = C.in_conv;
+            C.in_tol2 = fmax(p.sweep_red * p.sweep_red * C.in_rr, 0.25 * eta2 / (sig * sig));
+        } else {
+            C.in_tol2 = p.inner_tol * p.inner_tol * C.rn2;
+            C.in_done = (C.in_rr <= C.in_tol2) ? 1 : 0;
+        }
         if (!C.in_done) atomicAnd(&all_done, 0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         p.ctl->k = 0;
         p.ctl->in_ctr = 0;
+        p.ctl->refine_now = 0;
         p.ctl->inner_done = all_done;
         if (p.in_graph) cudaGraphSetConditional(p.h_inner, (!all_done && p.inner_max > 0) ? 1u : 0u);
     }
@@ -608,6 +641,7 @@ __global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_inner_a(Panel<T> p) 
         if (!(dad > 0.0) || !isfinite(dad)) { // S not positive definite on this direction
             C.in_done = 1;
             C.in_alpha = 0.0;
+            if (C.in_rr > 1e-30) C.s_bad = 1;
             continue;
         }
         C.in_alpha = C.in_rr / dad;
@@ -624,6 +658,10 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
     const int k = p.ctl->k;
     const X *D = p.D[k & 1];
     T *Y = p.R[(p.ctl->n + 1) & 1];
+    // the first step of an FP32 sweep of the refinement starts its correction
+    // from zero (written here, not by the refinement pass: that pass still reads
+    // the previous correction of neighbouring rows while it runs)
+    const bool fresh = p.ir && k == 0;
     T a[CPT]; // inner CG step length (real)
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) a[cc] = (T)p.col[lane * CPT + cc].in_alpha;
@@ -637,7 +675,12 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
         cpx<X> d[B][CPT];
 #pragma unroll
         for (int i = 0; i < B; ++i) {
-            ld_row<T, W>(Y, br * B + i, lane, y[i]);
+            if (fresh) {
+#pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) y[i][cc] = mk<T>(0, 0);
+            } else {
+                ld_row<T, W>(Y, br * B + i, lane, y[i]);
+            }
             ld_dir<T, W>(D, br * B + i, lane, d[i]);
             ld_row<T, W>(p.Tv, br * B + i, lane, t[i]);
             ld_row<T, W>(p.Av, br * B + i, lane, av[i]);
@@ -681,7 +724,98 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
         p.ctl->inner_total += 1;
         p.ctl->inner_done = all_done;
         const int cont = (!all_done) && (p.ctl->in_ctr < p.inner_max);
-        if (p.in_graph) cudaGraphSetConditional(p.h_inner, cont ? 1u : 0u);
+        if (p.ir) {
+            // an FP32 sweep of the refinement: when it ends, the refinement kernel
+            // that follows in the loop body applies it (the loop condition is its)
+            if (!cont) p.ctl->refine_now = 1;
+        } else if (p.in_graph) {
+            cudaGraphSetConditional(p.h_inner, cont ? 1u : 0u);
+        }
+    }
+}
+
+// ------------------------------------------ inner solve by refinement (df): R
+// After an FP32 sweep has solved S c = t (from c = 0, to its own tolerance):
+// y += c, t -= S c (a df product with the FP32 operand c, so t stays the true
+// residual rt - S y to df rounding) and the next sweep's FP32 residual t32 = t.
+// c is read here as a neighbour operand by every CTA, so this pass leaves it
+// as it is; the next sweep's first step overwrites it.  The last CTA ends the inner solve of every column whose ||t|| is below
+// inner_tol ||rt|| (or that reached refine_max refinements) and sets the loop
+// condition; the kernel returns at once in the loop iterations in which the
+// sweep goes on (refine_now == 0).
+template <typename T, int B, int W>
+__global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_refine(Panel<T> p) {
+    if constexpr (std::is_same<T, df>::value) {
+        if (!p.ctl->refine_now) return;
+        using TM = Teams<df, W, NT>;
+        const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
+        df *Y = p.R[(p.ctl->n + 1) & 1];
+        LdF32<W> ld{p.C32, lane};
+        // the sweep solved S c' = t / sig: c = sig c'; the next sweep sees t / ||t_old||
+        const ColState &Cl = p.col[lane];
+        const df sig = df(Cl.in_sig);
+        const float inv_new = (float)(1.0 / safe_scale(Cl.in_t2));
+        Acc<df> acc[1][1];
+        acc[0][0].zero();
+        const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
+        for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
+            cpx<df> sc[B][1];
+            bsr_row_product<df, B, float>(p.s_rp, p.s_ci, p.s_val, br, ld, sc, p.s_unit ? br : -1);
+#pragma unroll
+            for (int i = 0; i < B; ++i) {
+                const int64_t row = br * B + i;
+                cpx<df> y[1], t[1];
+                cpx<float> c[1];
+                ld_row<df, W>(Y, row, lane, y);
+                ld_row<df, W>(p.Tv, row, lane, t);
+                ld(row, c);
+                y[0] = mk(fma_f(sig, c[0].re, y[0].re), fma_f(sig, c[0].im, y[0].im));
+                t[0] = mk(t[0].re - sig * sc[i][0].re, t[0].im - sig * sc[i][0].im);
+                acc[0][0].add(t[0].re * t[0].re);
+                acc[0][0].add(t[0].im * t[0].im);
+                st_row<df, W>(Y, row, lane, y);
+                st_row<df, W>(p.Tv, row, lane, t);
+                const int64_t o = (row * W + lane) * 2;
+                *reinterpret_cast<float2 *>(p.T32 + o) = make_float2(t[0].re.hi * inv_new, t[0].im.hi * inv_new);
+            }
+        }
+        cta_partials<df, W, NT, 1>(acc, p.part);
+        if (!last_cta_arrival(&p.ctl->arrive)) return;
+        __shared__ double red[W];
+        reduce_partials<df, W, NT, 1>(p.part, red);
+        __shared__ int any;
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        for (int c = threadIdx.x; c < W; c += NT) {
+            ColState &C = p.col[c];
+            if (C.done || !C.in_sweep) continue;
+            const double t2 = red[c];
+            const double eta2 = p.inner_tol * p.inner_tol * C.rn2;
+            const double sig = safe_scale(C.in_t2); // the scale the rows used for the next sweep
+            C.in_refines += 1;
+            C.in_t2 = t2;
+            if (!(t2 > eta2) || !isfinite(t2) || C.in_refines >= p.refine_max || C.s_bad) {
+                C.in_sweep = 0;
+                C.in_conv = 1;
+                C.in_done = 1;
+                continue;
+            }
+            C.in_sig = sig;
+            C.in_rr = t2 / (sig * sig);
+            C.in_alpha = 0.0;
+            C.in_beta = 0.0;
+            C.in_tol2 = fmax(p.sweep_red * p.sweep_red * C.in_rr, 0.25 * eta2 / (sig * sig));
+            C.in_done = 0;
+            atomicOr(&any, 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            p.ctl->k = 0;
+            p.ctl->in_ctr = 0;
+            p.ctl->refine_now = 0;
+            p.ctl->refine_total += 1;
+            if (p.in_graph) cudaGraphSetConditional(p.h_inner, any ? 1u : 0u);
+        }
     }
 }
 
@@ -752,8 +886,9 @@ __global__ void k_writeout(Panel<T> p) {
     }
     if (last_cta_arrival(&p.ctl->arrive) && threadIdx.x == 0) {
         if (p.stats) {
-            p.stats[2 * panel] = p.ctl->iter_ctr;
-            p.stats[2 * panel + 1] = p.ctl->inner_total;
+            p.stats[3 * panel] = p.ctl->iter_ctr;
+            p.stats[3 * panel + 1] = p.ctl->inner_total;
+            p.stats[3 * panel + 2] = p.ctl->refine_total;
         }
         p.ctl->panel = panel + 1;
     }
@@ -818,6 +953,7 @@ struct SolveLaunch {
     double *ms_out;   // [8] average ms per launch (profile)
     Panel<double> pd; // type-erased panel (all T-dependent members are pointers)
     int ncta_a = 0;   // grid of IC_A and C (0: ncta): they fit one more CTA per SM than the others
+    int ncta_f = 0;   // grid of the FP32 sweep kernels of the refinement (df panels with S)
     int rc = TB_OK;
 
     int vec_grid(int W) const {
@@ -835,23 +971,60 @@ struct SolveLaunch {
             solve_graph<T, B, W>(p);
     }
 
+    // The FP32 sweeps of the refinement run the FP32 inner CG kernels on this
+    // view of a df panel: their solution is the sweep correction c, their
+    // residual the FP32 sweep residual, their product a = S d with S's FP32
+    // values; the column states are the df panel's own.
+    template <typename T>
+    static Panel<float> fp32_view(const Panel<T> &p) {
+        Panel<float> f;
+        std::memcpy(&f, &p, sizeof(f));
+        f.h_val = nullptr;
+        f.s_val = p.s_val32;
+        f.R[0] = f.R[1] = p.C32;
+        f.Tv = p.T32;
+        f.Av = p.A32;
+        f.RT = f.P[0] = f.P[1] = f.SP = f.U = f.HP = nullptr;
+        for (int k = 0; k < 2; ++k) f.D[k] = reinterpret_cast<float *>(p.D[k]);
+        return f;
+    }
+
     template <typename T, int B, int W>
     void profile(Panel<T> p) {
         p.in_graph = 0;
-        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta);
+        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta), grid_f(ncta_f > 0 ? ncta_f : ncta);
         const int has_s_i = has_s ? 1 : 0;
+        const bool ir = p.ir != 0;
+        Panel<float> pf = fp32_view(p);
+        // one inner iteration: the df inner CG pair, or an FP32 sweep step of the refinement
+        auto inner_a = [&]() {
+            if constexpr (std::is_same<T, df>::value)
+                if (ir) return (void)k_inner_a<float, B, W><<<grid_f, block, 0, stream>>>(pf);
+            k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
+        };
+        auto inner_b = [&]() {
+            if constexpr (std::is_same<T, df>::value)
+                if (ir) return (void)k_inner_b<float, B, W><<<grid_f, block, 0, stream>>>(pf);
+            k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
+        };
+        // a refinement pass with its work done (outside the graph nothing sets refine_now)
+        auto refine = [&]() {
+            cudaMemsetAsync(&p.ctl->refine_now, 1, 1, stream);
+            k_refine<T, B, W><<<grid, block, 0, stream>>>(p);
+        };
         k_init_state<T, W><<<1, NT, 0, stream>>>(p, has_s_i);
         k_init_vec<T, W><<<vec_grid(W), NT, 0, stream>>>(p, n_rows, has_s_i);
         if (has_s) {
             k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
-            k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
-            k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
+            inner_a();
+            inner_b();
+            if (ir) refine();
             k_rho<T, B, W><<<grid_a, block, 0, stream>>>(p, 1);
         }
-        // events: [0] A [1] B [2] (untimed first inner pair) [3] IC_A [4] IC_B [5] C [6]
-        cudaEvent_t ev[7];
+        // events: [0] A [1] B [2] (untimed first inner pair) [3] IC_A [4] IC_B [5] R [6] C [7]
+        cudaEvent_t ev[8];
         for (auto &e : ev) cudaEventCreate(&e);
-        double acc[5] = {0, 0, 0, 0, 0};
+        double acc[6] = {0, 0, 0, 0, 0, 0};
         for (int r = 0; r < profile_reps && !rc; ++r) {
             cudaEventRecord(ev[0], stream);
             if (has_s)
@@ -868,25 +1041,27 @@ struct SolveLaunch {
             if (has_s) {
                 // first inner iteration (no previous direction) untimed; time a
                 // steady-state one (k = 1), as most inner iterations of a solve are
-                k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
-                k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
+                inner_a();
+                inner_b();
                 cudaEventRecord(ev[3], stream);
-                k_inner_a<T, B, W><<<grid_a, block, 0, stream>>>(p);
+                inner_a();
                 cudaEventRecord(ev[4], stream);
-                k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
+                inner_b();
                 cudaEventRecord(ev[5], stream);
-                k_rho<T, B, W><<<grid_a, block, 0, stream>>>(p, 0);
+                if (ir) refine();
                 cudaEventRecord(ev[6], stream);
-                last = 6;
+                k_rho<T, B, W><<<grid_a, block, 0, stream>>>(p, 0);
+                cudaEventRecord(ev[7], stream);
+                last = 7;
             }
             cudaError_t e = cudaEventSynchronize(ev[last]);
             if (e != cudaSuccess) {
                 rc = set_error(ctx, TB_ERR_CUDA, "profile: %s", cudaGetErrorString(e));
                 break;
             }
-            // (kernel, start event, end event)
-            const int spans[5][3] = {{0, 0, 1}, {1, 1, 2}, {2, 3, 4}, {3, 4, 5}, {4, 5, 6}};
-            for (int q = 0; q < (has_s ? 5 : 2); ++q) {
+            // (kernel slot, start event, end event)
+            const int spans[6][3] = {{0, 0, 1}, {1, 1, 2}, {2, 3, 4}, {3, 4, 5}, {4, 6, 7}, {5, 5, 6}};
+            for (int q = 0; q < (has_s ? 6 : 2); ++q) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, ev[spans[q][1]], ev[spans[q][2]]);
                 acc[spans[q][0]] += ms;
@@ -894,8 +1069,9 @@ struct SolveLaunch {
         }
         for (auto &e : ev) cudaEventDestroy(e);
         for (int k = 0; k < 8; ++k) ms_out[k] = 0.0;
-        for (int k = 0; k < 5; ++k) ms_out[k] = acc[k] / profile_reps;
+        for (int k = 0; k < 6; ++k) ms_out[k] = acc[k] / profile_reps;
         if (!has_s) ms_out[2] = ms_out[3] = ms_out[4] = 0.0;
+        if (!ir) ms_out[5] = 0.0;
     }
 
     template <typename T, int B, int W>
@@ -909,45 +1085,60 @@ struct SolveLaunch {
         }
         p.h_outer = gb.handle(g, 1u, cudaGraphCondAssignDefault);
         cudaGraphConditionalHandle h_inner_init = has_s ? gb.handle(g, 0u, 0u) : 0;
-        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta);
+        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta), grid_f(ncta_f > 0 ? ncta_f : ncta);
+        const bool ir = p.ir != 0;
         int has_s_i = has_s ? 1 : 0;
         int init1 = 1, init0 = 0;
         int64_t nr = n_rows;
         // kernel arguments are copied when each node is added
         Panel<T> p_init = p;
         p_init.h_inner = h_inner_init;
+        Panel<float> pf_init = fp32_view(p_init);
         void *a_state[] = {&p, &has_s_i};
         void *a_vec[] = {&p, &nr, &has_s_i};
         cudaGraphNode_t n_state = gb.add_kernel(g, (const void *)k_init_state<T, W>, dim3(1), block, a_state, nullptr, 0);
         cudaGraphNode_t last = gb.add_kernel(g, (const void *)k_init_vec<T, W>, dim3(vec_grid(W)), block, a_vec, &n_state, 1);
         void *a_pinit[] = {&p_init};
+        void *a_finit[] = {&pf_init};
         void *a_pinit_rho[] = {&p_init, &init1};
+        // body of an inner loop: the df inner CG pair, or an FP32 sweep step and
+        // the refinement pass that applies a finished sweep
+        auto inner_body = [&](cudaGraph_t ib, void **a_t, void **a_f) {
+            if constexpr (std::is_same<T, df>::value) {
+                if (ir) {
+                    cudaGraphNode_t y = gb.add_kernel(ib, (const void *)k_inner_a<float, B, W>, grid_f, block, a_f, nullptr, 0);
+                    y = gb.add_kernel(ib, (const void *)k_inner_b<float, B, W>, grid_f, block, a_f, &y, 1);
+                    gb.add_kernel(ib, (const void *)k_refine<T, B, W>, grid, block, a_t, &y, 1);
+                    return;
+                }
+            }
+            (void)a_f;
+            cudaGraphNode_t y = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid_a, block, a_t, nullptr, 0);
+            gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_t, &y, 1);
+        };
         if (has_s) {
             last = gb.add_kernel(g, (const void *)k_update_S<T, B, W>, grid, block, a_pinit, &last, 1);
             cudaGraph_t ib = nullptr;
             last = gb.add_while(g, h_inner_init, &last, 1, &ib);
-            if (!gb.rc) {
-                cudaGraphNode_t x = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid_a, block, a_pinit, nullptr, 0);
-                gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_pinit, &x, 1);
-            }
+            if (!gb.rc) inner_body(ib, a_pinit, a_finit);
             last = gb.add_kernel(g, (const void *)k_rho<T, B, W>, grid_a, block, a_pinit_rho, &last, 1);
         }
         cudaGraph_t ob = nullptr;
         cudaGraphNode_t outer = gb.add_while(g, p.h_outer, &last, 1, &ob);
         Panel<T> p_body = p;
+        Panel<float> pf_body;
         void *a_body[] = {&p_body};
+        void *a_fbody[] = {&pf_body};
         void *a_body_rho[] = {&p_body, &init0};
         if (!gb.rc) {
             if (has_s) {
                 p_body.h_inner = gb.handle(ob, 0u, 0u);
+                pf_body = fp32_view(p_body);
                 cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, true>, grid, block, a_body, nullptr, 0);
                 x = gb.add_kernel(ob, (const void *)k_update_S<T, B, W>, grid, block, a_body, &x, 1);
                 cudaGraph_t ib = nullptr;
                 x = gb.add_while(ob, p_body.h_inner, &x, 1, &ib);
-                if (!gb.rc) {
-                    cudaGraphNode_t y = gb.add_kernel(ib, (const void *)k_inner_a<T, B, W>, grid_a, block, a_body, nullptr, 0);
-                    gb.add_kernel(ib, (const void *)k_inner_b<T, B, W>, grid, block, a_body, &y, 1);
-                }
+                if (!gb.rc) inner_body(ib, a_body, a_fbody);
                 gb.add_kernel(ob, (const void *)k_rho<T, B, W>, grid_a, block, a_body_rho, &x, 1);
             } else {
                 cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, false>, grid, block, a_body, nullptr, 0);

@@ -44,8 +44,21 @@ struct ColState {
     double chk_w;   // worst active shift residual at the last stagnation check
     int32_t chk_n;  // iteration of that check (-1: none yet)
     int32_t restarts, restart; // restarts so far; 1 while a restart is in flight
+    int32_t s_bad;  // the inner CG met a direction with d^H S d <= 0 (S not positive definite)
+    // inner solve by refinement (df panels): the true residual t = rt - S y in df,
+    // FP32 CG sweeps on S c = t, y += c after each sweep
+    int32_t in_sweep;   // 1 while this column's inner solve is still refining
+    int32_t in_conv;    // 1 once ||t|| <= inner_tol ||rt|| (or the refinement cap is reached)
+    int32_t in_refines; // refinements made in this outer iteration
     int32_t pad_;
+    double in_t2;       // ||t||^2 of the true residual at the last refinement
+    double in_sig;      // scale of the current FP32 sweep: it solves S c' = t / in_sig
 };
+
+// A residual norm usable as a scale (1 when it is zero or not finite).
+__host__ __device__ __forceinline__ double safe_scale(double norm2) {
+    return (norm2 > 1e-300 && norm2 < 1e300) ? sqrt(norm2) : 1.0;
+}
 
 struct ShiftState {
     c64 pi, pi_prev, pi_next; // pi_{n-1}, pi_{n-2}, pi_n at the start of A(n)
@@ -64,7 +77,10 @@ struct Ctrl {
     int32_t in_ctr;       // inner loop executions in this outer iteration (hard cap)
     int32_t panel;        // index of the panel being solved
     int64_t inner_total;  // inner iterations summed over the panel
-    int64_t pad[4];
+    int64_t refine_total; // refinement passes (df panels) summed over the panel
+    int32_t refine_now;   // set by the last FP32 sweep step: the next refinement kernel does its work
+    int32_t pad32;
+    int64_t pad[2];
 };
 
 // Vectors of the inner CG on S that only steer it: its search direction d and
@@ -97,6 +113,13 @@ struct Panel {
     T *R[2], *RT, *P[2], *SP, *U, *Tv, *Av;
     T *HP;                         // H p_n by recurrence (FP64 and df panels; null for FP32)
     typename DirOf<T>::type *D[2]; // inner CG directions (FP32 for df panels)
+    // inner solve by refinement (df panels with S): FP32 sweep residual, sweep
+    // correction and product S d, and an FP32 copy of S's values
+    float *T32, *C32, *A32;
+    const float *s_val32;
+    int32_t ir;          // 1: the inner solve on S runs as FP32 sweeps with df refinement
+    int32_t refine_max;  // refinements per outer iteration at most
+    double sweep_red;    // an FP32 sweep stops when its residual fell by this factor
     // state
     ColState *col;   // [W]
     ShiftState *sh;  // [W][nz]
@@ -131,7 +154,7 @@ struct Panel {
     int32_t *iters;
     double *resid;
     int32_t *status;
-    int64_t *stats;  // optional: [n_panels][2] = (outer iterations, inner iterations)
+    int64_t *stats;  // optional: [n_panels][3] = (outer iterations, inner iterations, refinements)
 };
 
 // ---------------------------------------------------------------- accumulators
@@ -374,6 +397,18 @@ struct LdDir {
                 x[c].im = fma_x(s[c], y[c].im, x[c].im);
             }
         }
+    }
+};
+
+// An FP32 complex panel read in the team layout of a df panel (one complex per
+// lane, float2): the correction of an FP32 sweep as the operand of a df product.
+template <int W>
+struct LdF32 {
+    const float *c;
+    int lane;
+    __device__ __forceinline__ void operator()(int64_t row, cpx<float> (&x)[1]) const {
+        const float2 v = *reinterpret_cast<const float2 *>(c + (row * W + lane) * 2);
+        x[0] = mk(v.x, v.y);
     }
 };
 
