@@ -256,19 +256,22 @@ def rel_errors(G, L, D, ptr, ref_G, ref_L, ref_D, ref_ptr):
     """Per-output relative errors of the solver's G, LDOS and DM against reference values.
 
     G: per (column, shift) the largest |dG| over the kept rows relative to the
-    largest |G_ref| of that column and shift; LDOS: per (column, shift) |dL| / |L_ref|;
-    DM: per column the largest |dD| relative to the largest |D_ref| of that column."""
-    eg, el, ed = [], [], []
+    largest |G_ref| of that column and shift; LDOS: per column the largest |dL|
+    over the shifts relative to the column's largest LDOS (and, as
+    "LDOS_per_shift", |dL| / |L_ref| per (column, shift), which is larger in the
+    spectral tails where the LDOS is small); DM: per column the largest |dD|
+    relative to the largest |D_ref| of that column."""
+    eg, el, els, ed = [], [], [], []
     for c in range(len(ref_ptr) - 1):
         g, gr = G[ptr[c]:ptr[c + 1]], ref_G[ref_ptr[c]:ref_ptr[c + 1]]
         eg.append(np.abs(g - gr).max(axis=0) / np.abs(gr).max(axis=0))
-        el.append(np.abs(L[c] - ref_L[c]) / np.abs(ref_L[c]))
+        el.append(np.abs(L[c] - ref_L[c]).max() / np.abs(ref_L[c]).max())
+        els.append(np.abs(L[c] - ref_L[c]) / np.abs(ref_L[c]))
         d, dr = D[ptr[c]:ptr[c + 1]], ref_D[ref_ptr[c]:ref_ptr[c + 1]]
         ed.append(np.abs(d - dr).max() / np.abs(dr).max())
-    eg, el, ed = np.concatenate(eg), np.concatenate(el), np.asarray(ed)
-    return {"G": {"max": float(eg.max()), "median": float(np.median(eg))},
-            "LDOS": {"max": float(el.max()), "median": float(np.median(el))},
-            "DM": {"max": float(ed.max()), "median": float(np.median(ed))}}
+    eg, el, els, ed = np.concatenate(eg), np.asarray(el), np.concatenate(els), np.asarray(ed)
+    stat = lambda a: {"max": float(a.max()), "median": float(np.median(a))}
+    return {"G": stat(eg), "LDOS": stat(el), "DM": stat(ed), "LDOS_per_shift": stat(els)}
 
 
 def golden_accuracy(res, panel_dev):

@@ -163,7 +163,8 @@ def test_local_df64_restarts_for_shifts_harder_than_the_seed(ctx):
         Ss = subspace.principal_submatrix(o.S, atoms)
         jl = int(np.searchsorted(atoms, rows[c] // b)) * b + int(rows[c] % b)
         ex = dense.green_lu(Hs.to_dense(), Ss.to_dense(), z, [jl])[[jl], 0, :]
-        assert rel_err_per_shift(G[optr[c]:optr[c + 1]], ex).max() < 1e-4   # the oracle at tol 1e-5: 2e-6..7e-6
+        # the FP64 oracle at tol 1e-5 is up to 6.9e-6 from dense LU on these columns
+        assert rel_err_per_shift(G[optr[c]:optr[c + 1]], ex).max() < 1e-5
 
 
 def test_local_order_does_not_change_results(ctx):
