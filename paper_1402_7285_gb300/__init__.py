@@ -22,14 +22,16 @@ from typing import Any, Optional
 import numpy as np
 
 from . import _lib
-from ._lib import (TB_COL_BREAKDOWN, TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_NONFINITE, TB_PREC_DF64,
-                   TB_PREC_FP64, TB_PREC_MIXED)
+from ._lib import (TB_COL_BREAKDOWN, TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_NONFINITE, TB_ERR_ARG,
+                   TB_ERR_SIZE, TB_ERR_STRUCTURE, TB_PREC_DF64, TB_PREC_FP64, TB_PREC_MIXED, TB_WARN_BREAKDOWN,
+                   TB_WARN_MAX_ITER, TB_WARN_NONFINITE)
 
 __all__ = ["Context", "Bsr", "TbError", "build_system", "bsr_spmm", "spmm_profile", "solve", "profile", "reduce_ldos_dm",
            "spec_to_c", "local_subspaces", "solve_local", "descriptors", "mlp_grad", "mlp_train", "mlp_predict",
            "mlp_param_count",
            "TB_PREC_FP64", "TB_PREC_MIXED", "TB_PREC_DF64", "TB_COL_CONVERGED", "TB_COL_MAX_ITER", "TB_COL_BREAKDOWN",
-           "TB_COL_NONFINITE"]
+           "TB_COL_NONFINITE", "TB_WARN_MAX_ITER", "TB_WARN_BREAKDOWN", "TB_WARN_NONFINITE", "TB_ERR_ARG",
+           "TB_ERR_SIZE", "TB_ERR_STRUCTURE"]
 
 
 class TbError(RuntimeError):

@@ -1,5 +1,7 @@
 """Multi-rank column sharding on CPU (gloo, world size 2): disjoint panels,
-every panel covered, and the max/sum reductions of the benchmark."""
+every panel covered, the max/sum reductions of the benchmark, and the gather
+of per-rank outputs (G, LDOS, DM of a test-only stub solver) into the layout
+a single rank produces."""
 import os
 import socket
 
@@ -9,7 +11,9 @@ torch = pytest.importorskip("torch")
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-from paper_1402_7285_gb300.sharding import panel_for, reduce_step_stats
+import numpy as np
+
+from paper_1402_7285_gb300.sharding import assemble_columns, gather_columns, panel_for, reduce_step_stats
 
 
 def _free_port():
@@ -20,6 +24,28 @@ def _free_port():
     return port
 
 
+N_PANELS, W, NZ = 6, 4, 3
+
+
+def _stub_panel(k):
+    """Outputs a solve of panel k would give (deterministic stand-in, no GPU):
+    column c keeps 2 + c % 3 rows, G = c + i*row + 1j*m, LDOS = c + m, DM = c - row."""
+    cols = np.arange(k * W, (k + 1) * W, dtype=np.int64)
+    rows = [np.arange(2 + c % 3) for c in cols]
+    ptr = np.zeros(W + 1, np.int64)
+    ptr[1:] = np.cumsum([len(r) for r in rows])
+    G = np.concatenate([(c + 10.0 * r)[:, None] + 1j * np.arange(NZ)[None, :] for c, r in zip(cols, rows)])
+    ldos = np.stack([c + np.arange(NZ, dtype=np.float64) for c in cols])
+    dm = np.concatenate([c - r.astype(np.float64) for c, r in zip(cols, rows)])
+    return {"cols": cols, "out_ptr": ptr, "G": G, "ldos": ldos, "dm": dm}
+
+
+def _local_part(rank, world):
+    mine = sorted({panel_for(s, rank, world, N_PANELS) for s in range(N_PANELS // world)})
+    parts = [_stub_panel(k) for k in mine]
+    return assemble_columns(parts)
+
+
 def _worker(rank, world, port, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -28,8 +54,11 @@ def _worker(rank, world, port, q):
     allp = [None] * world
     dist.all_gather_object(allp, mine)
     ms, pairs, launches = reduce_step_stats(10.0 + rank, 100.0 * (rank + 1), 7.0, world)
+    merged = gather_columns(_local_part(rank, world), world)
     if rank == 0:
-        q.put((allp, ms, pairs, launches))
+        q.put((allp, ms, pairs, launches, merged))
+    else:
+        assert merged is None
     dist.barrier()
     dist.destroy_process_group()
 
@@ -41,7 +70,7 @@ def test_two_ranks_gloo():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    allp, ms, pairs, launches = q.get(timeout=120)
+    allp, ms, pairs, launches, merged = q.get(timeout=120)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
@@ -49,6 +78,14 @@ def test_two_ranks_gloo():
     assert len(set(flat)) == len(flat) == 12          # disjoint panels
     assert sorted(flat) == list(range(12))           # steps 0..5 cover panels 0..11
     assert ms == 11.0 and pairs == 300.0 and launches == 14.0
+    single = assemble_columns([_stub_panel(k) for k in range(N_PANELS)])   # what one rank would hold
+    for key in ("cols", "out_ptr", "G", "ldos", "dm"):
+        assert np.array_equal(merged[key], single[key]), key
+
+
+def test_assemble_rejects_a_column_solved_twice():
+    with pytest.raises(ValueError):
+        assemble_columns([_stub_panel(0), _stub_panel(0)])
 
 
 def test_single_rank_is_identity():
