@@ -41,14 +41,14 @@ UNIT = "shift-RHS solves/s"
 WORKLOAD = wl.C2
 
 
-def workload_config(panel_w: int, precision: str, n_gpus: int) -> dict:
+def workload_config(panel_w: int, precision: str, n_gpus: int, cols_per_step: int = 0) -> dict:
     s = WORKLOAD.system
     return {
         "workload": f"{WORKLOAD.name}: SC {s.L}^3 periodic, 4 orbitals/atom (M={s.L ** 3 * s.bdim}), "
                     f"S=I+NN N(0,{s.s_param}), {WORKLOAD.n_shifts} shifts E+{WORKLOAD.eta}i on "
                     f"[{WORKLOAD.e_lo},{WORKLOAD.e_hi}], {WORKLOAD.n_rhs} RHS (orbital 0 of the 16^3 sub-block)",
         "tol": WORKLOAD.tol,
-        "rhs_per_step_per_gpu": panel_w,
+        "rhs_per_step_per_gpu": cols_per_step or panel_w,
         "panel_w": panel_w,
         "precision": precision,
         "parallelism": f"column shards x{n_gpus}",
@@ -316,6 +316,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     prec = {"mixed": tb.TB_PREC_MIXED, "fp64": tb.TB_PREC_FP64, "df64": tb.TB_PREC_DF64}[args.precision]
     W = args.panel_w
+    cps = args.columns_per_step or W                 # columns per step (a queue through W slots)
     Hh, Sh, _ = tb.build_system(WORKLOAD.system, WORKLOAD.seed)
     H, S = Hh.to(dev), Sh.to(dev)
     z = wl.shifts_of(WORKLOAD)
@@ -324,11 +325,11 @@ def run_ours(args, rank, world):
     E = z.real
     w_q = np.full(n_z, (WORKLOAD.e_hi - WORKLOAD.e_lo) / n_z)
     mu, kT = -2.0, 0.0
-    n_panels_total = len(rows_all) // W
+    n_panels_total = len(rows_all) // cps
 
     def panel(step):
         k = sharding.panel_for(step, rank, world, n_panels_total)
-        cols = rows_all[k * W:(k + 1) * W]
+        cols = rows_all[k * cps:(k + 1) * cps]
         ptr, orows = block_pattern_rows(Hh.row_ptr, Hh.col_idx, Hh.bdim, cols)
         return cols, ptr, orows
 
@@ -387,6 +388,10 @@ def run_ours(args, rank, world):
     outer = sum(r.outer_iters for r in results)
     inner = sum(r.inner_iters for r in results)
     refines = sum(r.refinements for r in results)
+    col_iters = sum(int(np.sum(r.iters.cpu().numpy())) for r in results)
+    # loop executions x slots against the iterations the columns needed: the work a
+    # panel spends on slots that wait for the queue's last columns
+    padded_work = (outer * W - col_iters) / max(col_iters, 1)
     # per panel: 13 set-up and write-out launches, A, B and C per outer iteration,
     # IC_A and IC_B per inner step and (df64 refinement) one R per inner step
     refine_mode = prec == tb.TB_PREC_DF64
@@ -480,7 +485,7 @@ def run_ours(args, rank, world):
     ctx.close()
     return {"value": value, "ms": ms_max, "pairs": pairs_all, "launches": launches_all, "clocks": clk.summary(),
             "e2e": e2e, "roofline": roof, "spmm": spmm, "outer_iters": outer, "inner_iters": inner, "fp64": fp64,
-            "refinements": refines, "accuracy": accuracy,
+            "refinements": refines, "accuracy": accuracy, "padded_work": padded_work,
             "iters_per_column": [int(x) for r in results for x in (r.iters.cpu().numpy() if hasattr(r.iters, "cpu")
                                                                     else r.iters)]}
 
@@ -636,6 +641,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--panel-w", type=int, default=32)
+    ap.add_argument("--columns-per-step", type=int, default=0,
+                    help="columns each step solves through the panel's slots (default: one panel width)")
     ap.add_argument("--precision", default="df64", choices=["df64", "mixed", "fp64"])
     ap.add_argument("--kernel-profile", action="store_true",
                     help="only launch the solver kernels of one panel (CUDA events; for ncu captures)")
@@ -719,11 +726,12 @@ def main():
     line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": out["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"mixed": "f32+f64", "df64": "df64 (f32 pairs)+f64", "fp64": "f64"}[args.precision],
-            "data": "synthetic", "config": workload_config(args.panel_w, args.precision, args.gpus),
+            "data": "synthetic", "config": workload_config(args.panel_w, args.precision, args.gpus,
+                                                           args.columns_per_step),
             "clocks": out["clocks"], "e2e": out["e2e"], "gpu_launches": int(out["launches"]),
             "roofline": out["roofline"], "spmm_hbm": out["spmm"], "cpu_baseline": cpu,
             "solver": {"outer_iters": out["outer_iters"], "inner_iters": out["inner_iters"],
-                       "refinements": out["refinements"],
+                       "refinements": out["refinements"], "padded_work": out["padded_work"],
                        "mean_iters_per_column": float(np.mean(out["iters_per_column"]))},
             "accuracy": out["accuracy"],
             "plain_fp64": out["fp64"]}

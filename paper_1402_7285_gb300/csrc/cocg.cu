@@ -115,36 +115,13 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     for (int64_t e = 0; e < n_out; ++e)
         TB_CHECK(ctx, h_orows[e] >= 0 && h_orows[e] < n_rows, TB_ERR_ARG, "out row out of range");
 
-    // ---- panels: consecutive columns, W per panel
+    // ---- one panel of W slots; the columns form a queue in the given order: a
+    // slot whose column finishes takes the next column (refill on the device)
     int W = opts.panel_w;
     if (W == 0) W = panel_width_for((int)std::min<int64_t>(n_rhs, mixed ? 64 : 32));
-    int n_panels = (int)((n_rhs + W - 1) / W);
-    std::vector<int64_t> pan_row((size_t)n_panels * W, -1), pan_dst((size_t)n_panels * W, -1);
-    std::vector<int32_t> pan_eptr((size_t)n_panels * (W + 1), 0);
-    std::vector<int64_t> pan_ebase(n_panels, 0);
-    int64_t max_ent = 1, max_col_ent = 1;
+    int64_t max_col_ent = 1;
     for (int64_t c = 0; c < n_rhs; ++c) max_col_ent = std::max<int64_t>(max_col_ent, h_optr[c + 1] - h_optr[c]);
     TB_CHECK(ctx, max_col_ent < (1 << 24), TB_ERR_SIZE, "too many kept rows in one column");
-    for (int pnl = 0; pnl < n_panels; ++pnl) {
-        const int64_t c0 = (int64_t)pnl * W;
-        pan_ebase[pnl] = h_optr[c0];
-        int64_t acc = 0;
-        for (int s = 0; s < W; ++s) {
-            const int64_t c = c0 + s;
-            pan_eptr[(size_t)pnl * (W + 1) + s] = (int32_t)acc;
-            if (c < n_rhs) {
-                pan_row[(size_t)pnl * W + s] = h_rhs[c];
-                pan_dst[(size_t)pnl * W + s] = c;
-                acc += h_optr[c + 1] - h_optr[c];
-                TB_CHECK(ctx, acc < INT32_MAX, TB_ERR_SIZE, "too many kept rows in one panel");
-            }
-        }
-        pan_eptr[(size_t)pnl * (W + 1) + W] = (int32_t)acc;
-        max_ent = std::max<int64_t>(max_ent, acc);
-    }
-    if (profiling) n_panels = 1;
-    std::vector<int64_t> ent_dst(std::max<int64_t>(n_out, 1));
-    for (int64_t e = 0; e < n_out; ++e) ent_dst[e] = e; // panels cover the columns in order
 
     // ---- stage caller arrays
     Stager stg(ctx, WS_STAGE_IN, stream);
@@ -224,13 +201,10 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const size_t o_ctl = take(sizeof(Ctrl));
     const size_t o_part = take(sizeof(double) * (size_t)W * 4 * ncta_max);
     const size_t o_zc = take(sizeof(c64) * n_z);
-    const size_t o_prow = take(sizeof(int64_t) * pan_row.size());
-    const size_t o_pdst = take(sizeof(int64_t) * pan_dst.size());
-    const size_t o_peptr = take(sizeof(int32_t) * pan_eptr.size());
-    const size_t o_pebase = take(sizeof(int64_t) * pan_ebase.size());
+    const size_t o_crow = take(sizeof(int64_t) * n_rhs);
+    const size_t o_cptr = take(sizeof(int64_t) * (n_rhs + 1));
     const size_t o_erow = take(sizeof(int64_t) * std::max<int64_t>(n_out, 1));
-    const size_t o_edst = take(sizeof(int64_t) * ent_dst.size());
-    const size_t o_stats = take(sizeof(int64_t) * 3 * n_panels);
+    const size_t o_stats = take(sizeof(int64_t) * 3);
     const size_t vsz = mixed ? sizeof(float) : sizeof(double);
     const size_t o_h32 = lowp ? take(vsz * H->nnzb * bb) : 0;
     const size_t o_s32 = (lowp && has_s) ? take(vsz * S->nnzb * bb) : 0;
@@ -240,18 +214,16 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     if (rc) return rc;
     char *sb = (char *)small_base;
     void *proj_base = nullptr;
-    rc = ws_get(ctx, WS_SOLVE_PROJ, sizeof(c64) * 2 * max_ent * n_z, &proj_base);
+    const int64_t proj_entries = (int64_t)W * max_col_ent * n_z; // one region of max_col_ent rows per slot
+    rc = ws_get(ctx, WS_SOLVE_PROJ, sizeof(c64) * 2 * proj_entries, &proj_base);
     if (rc) return rc;
 
     TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_ctl, 0, sizeof(Ctrl), stream));
-    TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_stats, 0, sizeof(int64_t) * 3 * n_panels, stream));
-    TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_prow, pan_row.data(), sizeof(int64_t) * pan_row.size(), cudaMemcpyHostToDevice, stream));
-    TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_pdst, pan_dst.data(), sizeof(int64_t) * pan_dst.size(), cudaMemcpyHostToDevice, stream));
-    TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_peptr, pan_eptr.data(), sizeof(int32_t) * pan_eptr.size(), cudaMemcpyHostToDevice, stream));
-    TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_pebase, pan_ebase.data(), sizeof(int64_t) * pan_ebase.size(), cudaMemcpyHostToDevice, stream));
+    TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_stats, 0, sizeof(int64_t) * 3, stream));
+    TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_crow, h_rhs.data(), sizeof(int64_t) * n_rhs, cudaMemcpyHostToDevice, stream));
+    TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_cptr, h_optr.data(), sizeof(int64_t) * (n_rhs + 1), cudaMemcpyHostToDevice, stream));
     if (n_out > 0)
         TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_erow, h_orows.data(), sizeof(int64_t) * n_out, cudaMemcpyHostToDevice, stream));
-    TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_edst, ent_dst.data(), sizeof(int64_t) * ent_dst.size(), cudaMemcpyHostToDevice, stream));
     k_copy_z<<<1, 256, 0, stream>>>((const double *)d_z, (c64 *)(sb + o_zc), n_z);
     const void *hval = d_hval, *sval = d_sval;
     if (lowp) {
@@ -308,16 +280,13 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.seed = seed;
     p.zs = mk(h_z[2 * seed], h_z[2 * seed + 1]);
     p.z = (const c64 *)(sb + o_zc);
-    p.max_ent = (int32_t)max_ent;
     p.max_col_ent = (int32_t)max_col_ent;
     p.xs = (c64 *)proj_base;
-    p.ps = (c64 *)proj_base + max_ent * n_z;
-    p.pan_row = (const int64_t *)(sb + o_prow);
-    p.pan_dst = (const int64_t *)(sb + o_pdst);
-    p.pan_ent_ptr = (const int32_t *)(sb + o_peptr);
-    p.pan_ent_base = (const int64_t *)(sb + o_pebase);
+    p.ps = (c64 *)proj_base + proj_entries;
+    p.col_row = (const int64_t *)(sb + o_crow);
+    p.col_ptr = (const int64_t *)(sb + o_cptr);
     p.ent_row = (const int64_t *)(sb + o_erow);
-    p.ent_dst = (const int64_t *)(sb + o_edst);
+    p.n_cols = n_rhs;
     p.part = sb + o_part;
     p.ctl = (Ctrl *)(sb + o_ctl);
     p.tol = opts.tol;
@@ -332,14 +301,16 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.sweep_red = 1e-5;
     p.max_iter = opts.max_iter;
     p.inner_max = opts.inner_max > 0 ? opts.inner_max : 40;
-    p.outer_cap = opts.max_iter + 2;
+    // loop executions: while the queue is not empty every slot is busy, so at most
+    // n_rhs (max_iter + 2) / W of them, then at most max_iter + 2 for the last columns
+    p.outer_cap = (n_rhs * ((int64_t)opts.max_iter + 2) + W - 1) / W + opts.max_iter + 2;
     p.G = (c64 *)d_G;
     p.iters = (int32_t *)d_iters;
     p.resid = (double *)d_resid;
     p.status = (int32_t *)d_status;
     p.stats = (int64_t *)(sb + o_stats);
 
-    SolveLaunch L{ctx, has_s, ncta, n_rows, n_panels, stream, profile_reps, ms};
+    SolveLaunch L{ctx, has_s, ncta, n_rows, stream, profile_reps, ms};
     L.pd = p;
     L.ncta_a = ncta_a;
     L.ncta_f = ncta_f;
@@ -351,13 +322,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     TB_CUDA_TRY(ctx, cudaGetLastError());
     if (profiling) return TB_OK;
     if (opts.stats) {
-        std::vector<int64_t> st3(3 * (size_t)n_panels);
-        TB_CUDA_TRY(ctx, cudaMemcpy(st3.data(), sb + o_stats, sizeof(int64_t) * st3.size(), cudaMemcpyDeviceToHost));
-        for (int i = 0; i < n_panels; ++i) {
-            opts.stats[0] += st3[3 * i];
-            opts.stats[1] += st3[3 * i + 1];
-            opts.stats[2] += st3[3 * i + 2];
-        }
+        TB_CUDA_TRY(ctx, cudaMemcpy(opts.stats, sb + o_stats, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost));
     }
     std::vector<int32_t> stv(n_rhs);
     TB_CUDA_TRY(ctx, cudaMemcpy(stv.data(), d_status, sizeof(int32_t) * n_rhs, cudaMemcpyDeviceToHost));

@@ -14,42 +14,65 @@ namespace tbgf {
 constexpr int NT = 256;
 
 // ------------------------------------------------------------------ init
+// Column state of a slot that starts column `col` of the queue (or an empty,
+// finished slot when the queue has no such column).
+template <typename T>
+__device__ ColState fresh_column(const Panel<T> &p, int64_t col) {
+    ColState C;
+    memset(&C, 0, sizeof(C));
+    C.alpha = mk(0.0, 0.0);
+    C.alpha_prev = mk(1.0, 0.0);
+    C.beta_prev = mk(0.0, 0.0);
+    C.rho = mk(1.0, 0.0); // S = I: rho_0 = e_j^T e_j; S != I: replaced by the init pass
+    C.rn2 = 1.0;
+    C.status = TB_COL_MAX_ITER;
+    C.n_active = p.nz;
+    C.in_done = 1;
+    C.zs = p.zs;
+    C.chk_n = -1;
+    if (col < p.n_cols) {
+        C.row = p.col_row[col];
+        C.dst = col;
+        C.ent0 = p.col_ptr[col];
+        C.n_ent = (int32_t)(p.col_ptr[col + 1] - C.ent0);
+    } else {
+        C.row = C.dst = -1;
+        C.done = 1;
+        C.n_active = 0;
+        C.rho = mk(0.0, 0.0);
+        C.rn2 = 0.0;
+        C.status = TB_COL_CONVERGED;
+    }
+    return C;
+}
+
+__device__ __forceinline__ ShiftState fresh_shift() {
+    ShiftState S;
+    S.pi = S.pi_prev = S.pi_next = mk(1.0, 0.0);
+    S.alpha_s = mk(0.0, 0.0);
+    S.resid = 1.0;
+    S.active = 1;
+    S.conv_it = -1;
+    return S;
+}
+
+// A restarting column (a stall restart, or a slot that took the next column of
+// the queue) starts its recurrences again with beta = 0: its previous direction
+// and the vectors kept by recurrence are cleared, so that nothing of the old
+// column (not even an inf or a NaN) survives the multiplication by zero.
+template <typename T, int W>
+__device__ __forceinline__ void clear_restart_row(const Panel<T> &p, int n, int64_t row, int col) {
+    const int64_t o = (row * W + col) * 2;
+    T *pp = p.P[n & 1];
+    pp[o] = pp[o + 1] = (T)0;
+    if (p.SP) p.SP[o] = p.SP[o + 1] = (T)0;
+    if (p.HP) p.HP[o] = p.HP[o + 1] = (T)0;
+}
+
 template <typename T, int W>
 __global__ void k_init_state(Panel<T> p, int has_s) {
-    const int panel = p.ctl->panel;
-    for (int c = threadIdx.x; c < W; c += blockDim.x) {
-        ColState C;
-        memset(&C, 0, sizeof(C));
-        C.row = p.pan_row[(int64_t)panel * W + c];
-        C.dst = p.pan_dst[(int64_t)panel * W + c];
-        C.alpha = mk(0.0, 0.0);
-        C.alpha_prev = mk(1.0, 0.0);
-        C.beta_prev = mk(0.0, 0.0);
-        C.rho = mk(1.0, 0.0); // S = I: rho_0 = e_j^T e_j; S != I: replaced by the init pass
-        C.rn2 = 1.0;
-        C.status = TB_COL_MAX_ITER;
-        C.n_active = p.nz;
-        if (C.row < 0) {
-            C.done = 1;
-            C.n_active = 0;
-            C.rho = mk(0.0, 0.0);
-            C.rn2 = 0.0;
-            C.status = TB_COL_CONVERGED;
-        }
-        C.in_done = 1;
-        C.zs = p.zs;
-        C.chk_n = -1;
-        p.col[c] = C;
-    }
-    for (int q = threadIdx.x; q < W * p.nz; q += blockDim.x) {
-        ShiftState S;
-        S.pi = S.pi_prev = S.pi_next = mk(1.0, 0.0);
-        S.alpha_s = mk(0.0, 0.0);
-        S.resid = 1.0;
-        S.active = 1;
-        S.conv_it = -1;
-        p.sh[q] = S;
-    }
+    for (int c = threadIdx.x; c < W; c += blockDim.x) p.col[c] = fresh_column(p, c);
+    for (int q = threadIdx.x; q < W * p.nz; q += blockDim.x) p.sh[q] = fresh_shift();
     if (threadIdx.x == 0) {
         p.ctl->arrive = 0;
         p.ctl->n = has_s ? 1 : 0;
@@ -58,6 +81,7 @@ __global__ void k_init_state(Panel<T> p, int has_s) {
         p.ctl->inner_done = 0;
         p.ctl->iter_ctr = 0;
         p.ctl->in_ctr = 0;
+        p.ctl->next_col = p.n_cols < W ? p.n_cols : W;
         p.ctl->inner_total = 0;
         p.ctl->refine_total = 0;
         p.ctl->refine_now = 0;
@@ -66,13 +90,12 @@ __global__ void k_init_state(Panel<T> p, int has_s) {
 
 template <typename T, int W>
 __global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
-    const int panel = p.ctl->panel;
     const int64_t total = n_rows * W;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += stride) {
         const int64_t row = t / W;
         const int c = (int)(t % W);
-        const int64_t j = p.pan_row[(int64_t)panel * W + c];
+        const int64_t j = p.col[c].row;
         const T one = (j == row) ? (T)1 : (T)0;
         const int64_t o = t * 2;
         p.RT[o] = one, p.RT[o + 1] = 0;
@@ -90,7 +113,7 @@ __global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
         }
         if (p.HP) p.HP[o] = p.HP[o + 1] = 0;
     }
-    const int64_t ne = (int64_t)p.max_ent * p.nz;
+    const int64_t ne = (int64_t)W * p.max_col_ent * p.nz;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ne; t += stride) {
         p.xs[t] = mk(0.0, 0.0);
         p.ps[t] = mk(0.0, 0.0);
@@ -118,9 +141,6 @@ template <typename T, int W>
 __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) {
     __shared__ c64 s_a[PAIR_CHUNK], s_b[PAIR_CHUNK];
     __shared__ int s_c[PAIR_CHUNK], s_m[PAIR_CHUNK], s_on[PAIR_CHUNK];
-    const int panel = p.ctl->panel;
-    const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
-    const int64_t ebase = p.pan_ent_base[panel];
     const int P = W * p.nz;
     const int q0 = (int)((int64_t)blockIdx.x * P / gridDim.x), q1 = (int)((int64_t)(blockIdx.x + 1) * P / gridDim.x);
     const int KM = p.max_col_ent;
@@ -156,12 +176,12 @@ __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) 
             const int t = (int)(i / KM), k = (int)(i % KM);
             if (!s_on[t]) continue;
             const int c = s_c[t], m = s_m[t];
-            const int e = eptr[c] + k;
-            if (e >= eptr[c + 1]) continue;
-            const int64_t row = p.ent_row[ebase + e];
+            const ColState &C = p.col[c];
+            if (k >= C.n_ent) continue;
+            const int64_t row = p.ent_row[C.ent0 + k];
             const T *rp = Rc + (row * W + c) * 2;
             const c64 rv = mk((double)rp[0], (double)rp[1]);
-            c64 *ps = p.ps + (int64_t)e * p.nz + m;
+            c64 *ps = p.ps + ((int64_t)c * KM + k) * p.nz + m;
             *ps = s_a[t] * rv + s_b[t] * (*ps);
         }
         __syncthreads();
@@ -173,8 +193,6 @@ template <typename T, int W>
 __device__ void pair_step_B(const Panel<T> &p) {
     __shared__ c64 s_a[PAIR_CHUNK];
     __shared__ int s_c[PAIR_CHUNK], s_m[PAIR_CHUNK], s_on[PAIR_CHUNK];
-    const int panel = p.ctl->panel;
-    const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
     const int P = W * p.nz;
     const int q0 = (int)((int64_t)blockIdx.x * P / gridDim.x), q1 = (int)((int64_t)(blockIdx.x + 1) * P / gridDim.x);
     const int KM = p.max_col_ent;
@@ -211,10 +229,9 @@ __device__ void pair_step_B(const Panel<T> &p) {
             const int t = (int)(i / KM), k = (int)(i % KM);
             if (!s_on[t]) continue;
             const int c = s_c[t], m = s_m[t];
-            const int e = eptr[c] + k;
-            if (e >= eptr[c + 1]) continue;
-            c64 *xs = p.xs + (int64_t)e * p.nz + m;
-            *xs = *xs + s_a[t] * p.ps[(int64_t)e * p.nz + m];
+            if (k >= p.col[c].n_ent) continue;
+            const int64_t e = ((int64_t)c * KM + k) * p.nz + m;
+            p.xs[e] = p.xs[e] + s_a[t] * p.ps[e];
         }
         __syncthreads();
     }
@@ -298,8 +315,10 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
     cta_partials<T, W, NT, 2>(acc, p.part);
     pair_step_A<T, W>(p, Rc, n);
     if (!last_cta_arrival(&p.ctl->arrive)) return;
-    // ---- last CTA: alpha_n = rho_n / mu_n; column and panel completion
+    // ---- last CTA: alpha_n = rho_n / mu_n; column completion, retire and refill
     __shared__ double red[W * 2];
+    __shared__ int fin[W], n_fin; // slots whose column finished in this iteration
+    if (threadIdx.x == 0) n_fin = 0;
     reduce_partials<T, W, NT, 2>(p.part, red);
     for (int c = threadIdx.x; c < W; c += NT) {
         ColState &C = p.col[c];
@@ -326,9 +345,60 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
             C.done = 1;
             C.status = st;
             C.alpha = mk(0.0, 0.0);
+            fin[atomicAdd(&n_fin, 1)] = c;
         } else {
             C.alpha = a;
         }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) // slots take the queue's columns in slot order (deterministic)
+        for (int f = 1; f < n_fin; ++f)
+            for (int g = f; g > 0 && fin[g - 1] > fin[g]; --g) {
+                const int x = fin[g];
+                fin[g] = fin[g - 1];
+                fin[g - 1] = x;
+            }
+    __syncthreads();
+    if (n_fin > 0) {
+        // retire: the finished columns' results go out now, so that their slots
+        // can take the next columns of the queue in this same iteration
+        const int KM = p.max_col_ent;
+        for (int f = 0; f < n_fin; ++f) {
+            const ColState &C = p.col[fin[f]];
+            const int64_t base = (int64_t)fin[f] * KM * p.nz, ne = (int64_t)C.n_ent * p.nz;
+            for (int64_t t = threadIdx.x; t < ne; t += NT) p.G[C.ent0 * p.nz + t] = p.xs[base + t];
+            for (int m = threadIdx.x; m < p.nz; m += NT)
+                p.resid[C.dst * p.nz + m] = p.sh[(int64_t)fin[f] * p.nz + m].resid;
+        }
+        __syncthreads();
+        // refill: the next column starts through the restart path (alpha = 0 this
+        // iteration, B / B' set its rt to e_j and clear its old directions, C
+        // starts its recurrences); the restart iteration is not counted
+        for (int f = threadIdx.x; f < n_fin; f += NT) {
+            ColState &C = p.col[fin[f]];
+            p.iters[C.dst] = C.iters;
+            p.status[C.dst] = C.status;
+            const int64_t next = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&p.ctl->next_col), 1ull);
+            ColState N = fresh_column(p, next);
+            if (N.dst >= 0) {
+                N.restart = 1;
+                N.fresh = 1;
+                N.iters = -1;
+            }
+            C = N;
+        }
+        __syncthreads();
+        for (int f = 0; f < n_fin; ++f) {
+            const int c = fin[f];
+            if (p.col[c].dst < 0) continue; // the queue is empty: the slot stays idle
+            for (int m = threadIdx.x; m < p.nz; m += NT) p.sh[(int64_t)c * p.nz + m] = fresh_shift();
+            const int64_t base = (int64_t)c * KM * p.nz;
+            for (int64_t t = threadIdx.x; t < (int64_t)KM * p.nz; t += NT) {
+                p.xs[base + t] = mk(0.0, 0.0);
+                p.ps[base + t] = mk(0.0, 0.0);
+            }
+        }
+        __syncthreads();
     }
     // Restart (df panels): a shift's residual is the seed's divided by |pi|, so
     // a shift much harder than the seed needs the seed residual below what df
@@ -338,8 +408,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
     // this iteration, B / B' reset rt to e_j, C restarts the recurrences;
     // converged shifts keep their solutions, active ones start from zero.
     if (p.stall2 > 0.0) {
-        const int panel = p.ctl->panel;
-        const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
+        const int KM = p.max_col_ent;
         for (int c = threadIdx.x; c < W; c += NT) {
             ColState &C = p.col[c];
             if (C.done || !(C.rn2 < p.stall2) || C.restarts >= 2) continue;
@@ -366,9 +435,9 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
                 if (!S.active) continue;
                 S.pi = S.pi_prev = S.pi_next = mk(1.0, 0.0);
                 S.resid = 1.0;
-                for (int e = eptr[c]; e < eptr[c + 1]; ++e) {
-                    p.xs[(int64_t)e * p.nz + m] = mk(0.0, 0.0);
-                    p.ps[(int64_t)e * p.nz + m] = mk(0.0, 0.0);
+                for (int k = 0; k < C.n_ent; ++k) {
+                    p.xs[((int64_t)c * KM + k) * p.nz + m] = mk(0.0, 0.0);
+                    p.ps[((int64_t)c * KM + k) * p.nz + m] = mk(0.0, 0.0);
                 }
             }
         }
@@ -397,6 +466,7 @@ __device__ void finish_outer(const Panel<T> &p, const double *rho_next, int init
             C.alpha_prev = mk(1.0, 0.0);
             C.rho = rn;
             C.restart = 0;
+            C.fresh = 0;
             C.iters += 1;
             continue;
         }
@@ -445,10 +515,12 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_sI(Panel<T> p) 
             ld_row<T, W>(p.U, row, lane, u);
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
-                if (rst >> cc & 1u)
+                if (rst >> cc & 1u) {
                     rt[cc] = mk<T>(row == p.col[lane * CPT + cc].row ? (T)1 : (T)0, 0);
-                else
+                    clear_restart_row<T, W>(p, p.ctl->n, row, lane * CPT + cc);
+                } else {
                     rt[cc] = rt[cc] - a[cc] * u[cc];
+                }
                 const T rr = rt[cc].re * rt[cc].re, ii = rt[cc].im * rt[cc].im;
                 acc[cc][0].add(rr);
                 acc[cc][0].add(-ii);
@@ -500,6 +572,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
         const c64 al = C.alpha;
         a[cc] = cvt<T>(al);
         ld.s[cc] = mk((X)(-al.re), (X)(-al.im));
+        ld.fresh_row[cc] = C.fresh ? C.row : -1;
         rst |= (C.restart ? 1u : 0u) << cc;
         if (cc == 0) inv_sig = (float)(1.0 / (C.restart ? 1.0 : safe_scale(C.rn2)));
     }
@@ -521,10 +594,12 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_update_S(Panel<T> p) {
 #pragma unroll
             for (int cc = 0; cc < CPT; ++cc) {
                 y0[cc] = mk((T)g[cc].re, (T)g[cc].im);
-                if (rst >> cc & 1u)
+                if (rst >> cc & 1u) {
                     rt[cc] = mk<T>(row == p.col[lane * CPT + cc].row ? (T)1 : (T)0, 0);
-                else
+                    clear_restart_row<T, W>(p, n, row, lane * CPT + cc);
+                } else {
                     rt[cc] = rt[cc] - a[cc] * u[cc];
+                }
                 t[cc] = rt[cc] - sy[i][cc];
                 acc[cc][0].add(rt[cc].re * rt[cc].re);
                 acc[cc][0].add(rt[cc].im * rt[cc].im);
@@ -859,23 +934,22 @@ __global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_rho(Panel<T> p, int 
 }
 
 // -------------------------------------------------------------- write-out
+// Results of the columns still in their slots when the loop ends (columns that
+// finished earlier were written when they retired).
 template <typename T, int W>
 __global__ void k_writeout(Panel<T> p) {
-    const int panel = p.ctl->panel;
-    const int32_t *eptr = p.pan_ent_ptr + (int64_t)panel * (W + 1);
-    const int64_t ebase = p.pan_ent_base[panel];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t ne = (int64_t)eptr[W] * p.nz;
-    for (int64_t t = tid; t < ne; t += stride) {
-        const int64_t e = t / p.nz;
-        const int m = (int)(t % p.nz);
-        p.G[p.ent_dst[ebase + e] * p.nz + m] = p.xs[t];
+    const int64_t per_slot = (int64_t)p.max_col_ent * p.nz;
+    for (int64_t t = tid; t < W * per_slot; t += stride) {
+        const ColState &C = p.col[t / per_slot];
+        const int64_t r = t % per_slot;
+        if (C.dst < 0 || r >= (int64_t)C.n_ent * p.nz) continue;
+        p.G[C.ent0 * p.nz + r] = p.xs[t];
     }
     for (int64_t q = tid; q < (int64_t)W * p.nz; q += stride) {
-        const int c = (int)(q / p.nz), m = (int)(q % p.nz);
-        const int64_t dst = p.col[c].dst;
-        if (dst >= 0) p.resid[dst * p.nz + m] = p.sh[q].resid;
+        const int64_t dst = p.col[q / p.nz].dst;
+        if (dst >= 0) p.resid[dst * p.nz + q % p.nz] = p.sh[q].resid;
     }
     if (tid < W) {
         const ColState &C = p.col[tid];
@@ -884,13 +958,10 @@ __global__ void k_writeout(Panel<T> p) {
             p.status[C.dst] = C.done ? C.status : TB_COL_MAX_ITER;
         }
     }
-    if (last_cta_arrival(&p.ctl->arrive) && threadIdx.x == 0) {
-        if (p.stats) {
-            p.stats[3 * panel] = p.ctl->iter_ctr;
-            p.stats[3 * panel + 1] = p.ctl->inner_total;
-            p.stats[3 * panel + 2] = p.ctl->refine_total;
-        }
-        p.ctl->panel = panel + 1;
+    if (last_cta_arrival(&p.ctl->arrive) && threadIdx.x == 0 && p.stats) {
+        p.stats[0] = p.ctl->iter_ctr;
+        p.stats[1] = p.ctl->inner_total;
+        p.stats[2] = p.ctl->refine_total;
     }
 }
 
@@ -947,7 +1018,6 @@ struct SolveLaunch {
     bool has_s;
     int ncta;
     int64_t n_rows;
-    int n_panels;
     cudaStream_t stream;
     int profile_reps; // > 0: time the kernels of the first panel instead of solving
     double *ms_out;   // [8] average ms per launch (profile)
@@ -1159,10 +1229,8 @@ struct SolveLaunch {
             cudaGraphDestroy(g);
             return;
         }
-        for (int i = 0; i < n_panels && !rc; ++i) {
-            e = cudaGraphLaunch(exec, stream);
-            if (e != cudaSuccess) rc = set_error(ctx, TB_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
-        }
+        e = cudaGraphLaunch(exec, stream);
+        if (e != cudaSuccess) rc = set_error(ctx, TB_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
         e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess && !rc) rc = set_error(ctx, TB_ERR_CUDA, "solve: %s", cudaGetErrorString(e));
         cudaGraphExecDestroy(exec);

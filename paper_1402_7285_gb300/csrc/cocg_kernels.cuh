@@ -39,7 +39,10 @@ struct ColState {
     double in_alpha, in_beta, in_tol2;
     int32_t done, status, iters, n_active, in_done, breakdown;
     int64_t row;    // right-hand side row j (-1: empty slot)
-    int64_t dst;    // global column index (-1: empty slot)
+    int64_t dst;    // column index of the solve (-1: empty slot, or results already written)
+    int64_t ent0;   // first kept-row entry of the column (index into G's rows)
+    int32_t n_ent;  // kept rows of the column
+    int32_t fresh;  // 1 from the moment a slot takes a new column until its first iteration ends
     c64 zs;         // this column's seed shift (changes on a restart)
     double chk_w;   // worst active shift residual at the last stagnation check
     int32_t chk_n;  // iteration of that check (-1: none yet)
@@ -73,9 +76,10 @@ struct Ctrl {
     int32_t k;            // inner iteration (buffer parity)
     int32_t panel_done;
     int32_t inner_done;
-    int32_t iter_ctr;     // outer loop executions (hard cap)
     int32_t in_ctr;       // inner loop executions in this outer iteration (hard cap)
-    int32_t panel;        // index of the panel being solved
+    int32_t pad0;
+    int64_t iter_ctr;     // outer loop executions (hard cap)
+    int64_t next_col;     // next column of the queue to load into a slot that retires
     int64_t inner_total;  // inner iterations summed over the panel
     int64_t refine_total; // refinement passes (df panels) summed over the panel
     int32_t refine_now;   // set by the last FP32 sweep step: the next refinement kernel does its work
@@ -127,16 +131,13 @@ struct Panel {
     int32_t seed;
     c64 zs;
     const c64 *z;    // [nz]
-    // kept rows (projection entries) of the current panel
-    int32_t max_ent;
-    c64 *xs, *ps;    // [max_ent][nz]
-    // panel descriptors for every panel (device)
-    const int64_t *pan_row;     // [n_panels][W]  rhs row per slot (-1 empty)
-    const int64_t *pan_dst;     // [n_panels][W]  global column per slot (-1 empty)
-    const int32_t *pan_ent_ptr; // [n_panels][W+1] kept-row ranges per slot (panel-local)
-    const int64_t *pan_ent_base;// [n_panels]      offset of the panel's entries
-    const int64_t *ent_row;     // [total entries] kept row
-    const int64_t *ent_dst;     // [total entries] row index into G
+    // kept rows (projection entries): a region of max_col_ent entries per slot
+    c64 *xs, *ps;    // [W][max_col_ent][nz]
+    // the column queue (device): columns are loaded into slots in this order
+    const int64_t *col_row;     // [n_cols]   right-hand side row j of each column
+    const int64_t *col_ptr;     // [n_cols+1] kept-row offsets (rows of G) of each column
+    const int64_t *ent_row;     // [col_ptr[n_cols]] kept rows
+    int64_t n_cols;
     // reductions
     void *part;      // [W*4][ncta] partials (double or float2)
     Ctrl *ctl;
@@ -146,7 +147,7 @@ struct Panel {
     double stall2;    // seed residual^2 below which a stagnating column restarts (0: never)
     int32_t max_iter;
     int32_t inner_max;
-    int32_t outer_cap;
+    int64_t outer_cap;
     int32_t in_graph; // 1: kernels run inside the solve graph and set its loop conditions
     int32_t max_col_ent; // largest number of kept rows of one column
     // outputs (device)
@@ -154,7 +155,7 @@ struct Panel {
     int32_t *iters;
     double *resid;
     int32_t *status;
-    int64_t *stats;  // optional: [n_panels][3] = (outer iterations, inner iterations, refinements)
+    int64_t *stats;  // [3] = (outer iterations, inner iterations, refinements)
 };
 
 // ---------------------------------------------------------------- accumulators
@@ -413,15 +414,24 @@ struct LdF32 {
 };
 
 // Starting guess of the inner CG, y_0 = r_n - alpha_n u (complex alpha per
-// column), formed in the direction type.
+// column), formed in the direction type; e_j for a column that a slot has just
+// taken from the queue (its r_n belongs to the slot's previous column).
 template <typename T, int W>
 struct LdGuess {
     typedef typename DirOf<T>::type X;
     const T *r;
     const T *u;
     cpx<X> s[PanelVec<T>::CPT]; // -alpha_n
+    int64_t fresh_row[PanelVec<T>::CPT]; // row j of a fresh column, -1 otherwise
     int lane;
     __device__ __forceinline__ void operator()(int64_t row, cpx<X> (&x)[PanelVec<T>::CPT]) const {
+        constexpr int CPT = PanelVec<T>::CPT;
+        guess(row, x);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            if (fresh_row[c] >= 0) x[c] = mk((X)(row == fresh_row[c] ? 1 : 0), (X)0);
+    }
+    __device__ __forceinline__ void guess(int64_t row, cpx<X> (&x)[PanelVec<T>::CPT]) const {
         constexpr int CPT = PanelVec<T>::CPT;
         if constexpr (std::is_same<T, df>::value) {
             cpx<df> rv[1], uv[1];
