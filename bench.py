@@ -177,6 +177,7 @@ def algorithmic_bytes(n_rows, nnzb, bdim, n_brows, W, n_z, n_ent, esz, dsz, refi
         out["IC_A_inner_S_product"] = 4 * V32 + Mb32    # T32, D_old in; D, A32 out; FP32 S
         out["IC_B_inner_update"] = 6 * V32              # C32, T32 rw; D, A32 in
         out["R_refine"] = 4 * V + 2 * V32 + Mb          # Y, T rw (df); C32 in, T32 out; df S
+        out["R_refine_fp32"] = 4 * V + 2 * V32 + Mb32   # the same with S c from FP32 values of S
     return out
 
 
@@ -388,6 +389,7 @@ def run_ours(args, rank, world):
     outer = sum(r.outer_iters for r in results)
     inner = sum(r.inner_iters for r in results)
     refines = sum(r.refinements for r in results)
+    light = sum(r.light_refinements for r in results)
     col_iters = sum(int(np.sum(r.iters.cpu().numpy())) for r in results)
     # loop executions x slots against the iterations the columns needed: the work a
     # panel spends on slots that wait for the queue's last columns
@@ -453,7 +455,8 @@ def run_ours(args, rank, world):
     prof = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W,
                       ctas_per_sm=args.ctas_per_sm)
     counts = {"A_outer_H_product": outer, "B_update": outer, "IC_A_inner_S_product": inner,
-              "IC_B_inner_update": inner, "C_rho": outer, "R_refine": refines}
+              "IC_B_inner_update": inner, "C_rho": outer, "R_refine": refines - light,
+              "R_refine_fp32": light}
     share = {k: prof[k] * counts[k] for k in prof if prof[k] > 0}
     dom = max(share, key=share.get)
     n_ent = int(ptr[-1].item())
@@ -485,7 +488,7 @@ def run_ours(args, rank, world):
     ctx.close()
     return {"value": value, "ms": ms_max, "pairs": pairs_all, "launches": launches_all, "clocks": clk.summary(),
             "e2e": e2e, "roofline": roof, "spmm": spmm, "outer_iters": outer, "inner_iters": inner, "fp64": fp64,
-            "refinements": refines, "accuracy": accuracy, "padded_work": padded_work,
+            "refinements": refines, "fp32_refinements": light, "accuracy": accuracy, "padded_work": padded_work,
             "iters_per_column": [int(x) for r in results for x in (r.iters.cpu().numpy() if hasattr(r.iters, "cpu")
                                                                     else r.iters)]}
 
@@ -731,7 +734,8 @@ def main():
             "clocks": out["clocks"], "e2e": out["e2e"], "gpu_launches": int(out["launches"]),
             "roofline": out["roofline"], "spmm_hbm": out["spmm"], "cpu_baseline": cpu,
             "solver": {"outer_iters": out["outer_iters"], "inner_iters": out["inner_iters"],
-                       "refinements": out["refinements"], "padded_work": out["padded_work"],
+                       "refinements": out["refinements"], "fp32_refinements": out["fp32_refinements"],
+                       "padded_work": out["padded_work"],
                        "mean_iters_per_column": float(np.mean(out["iters_per_column"]))},
             "accuracy": out["accuracy"],
             "plain_fp64": out["fp64"]}

@@ -146,7 +146,9 @@ int tb_build_csr(const tb_system_spec *spec, uint64_t seed, tb_bsr *H, tb_bsr *S
                            the residual t = rt - S y is kept in df, FP32 CG
                            sweeps solve S c = t (FP32 vectors, FP32 values of S,
                            two-float dot products) and each sweep's c is added
-                           to y in df, t -= S c with a df product, until
+                           to y in df, t -= S c with a df product (an FP32 one
+                           once every ||t|| <= 5e4 inner_tol ||rt||, where its
+                           error stays below inner_tol ||rt|| / 20), until
                            ||t|| <= inner_tol ||rt||                            */
 
 /* Y = A X for a real BSR matrix A (n = n_brows*bdim rows) and a complex panel
@@ -190,9 +192,10 @@ typedef struct {
                             with df panels and block edges <= 4 the inner S
                             product and the rho kernel run one more (at most 4) */
     void *stream;        /* cudaStream_t to queue work on                         */
-    int64_t *stats;      /* optional host array [3]: outer iterations, inner
-                            iterations and (DF64 with S) refinement passes summed
-                            over all panels (written before returning)            */
+    int64_t *stats;      /* optional host array [4]: outer iterations, inner
+                            iterations, and (DF64 with S) refinement passes and
+                            of those the ones that took S c in FP32 (written
+                            before returning)                                     */
 } tb_solve_opts;
 
 /* Fill `opts` with the defaults above. */
@@ -245,7 +248,8 @@ int shifted_cocg_solve(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const doub
  * state with a previous search direction).  ms[k] (k < 8) receives the average
  * milliseconds per launch of kernel k: 0 A (H product, shifted steps),
  * 1 B (residual update; with S also the S product of the inner start),
- * 2 IC_A (S product of the inner CG), 3 IC_B (inner CG update), 4 C (rho);
+ * 2 IC_A (S product of the inner CG), 3 IC_B (inner CG update), 4 C (rho),
+ * 5 R (DF64 with S: refinement pass with S c in df), 6 R with S c in FP32;
  * unused entries are 0.  These are the kernels the solve's graph runs. */
 int shifted_cocg_profile(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, int32_t n_z,
                          const int64_t *rhs_rows, int64_t n_rhs, const int64_t *out_row_ptr,

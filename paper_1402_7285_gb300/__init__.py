@@ -244,7 +244,8 @@ class SolveResult:
     rc: int       # 0 or OR of TB_WARN_*
     outer_iters: int = 0   # outer iterations summed over panels
     inner_iters: int = 0   # inner CG iterations summed over panels (S != I; df64: FP32 sweep steps)
-    refinements: int = 0   # refinement passes of the df64 inner solve summed over panels
+    refinements: int = 0   # refinement passes of the df64 inner solve
+    light_refinements: int = 0   # of those, passes that took S c in FP32
 
 
 def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_rows, *, tol=1e-10,
@@ -263,7 +264,7 @@ def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_
     iters = _empty((n_rhs,), np.int32, like)
     resid = _empty((n_rhs, n_z), np.float64, like)
     status = _empty((n_rhs,), np.int32, like)
-    stats = np.zeros(3, np.int64)
+    stats = np.zeros(4, np.int64)
     opts = _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, _stream_of(like), stats,
                  ctas_per_sm)
     Hc = H.c_struct()
@@ -272,7 +273,7 @@ def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_
                                     _ptr(zc), n_z, _ptr(rhs), n_rhs, _ptr(optr), _ptr(orows), ctypes.byref(opts),
                                     _ptr(G), _ptr(iters), _ptr(resid), _ptr(status))
     ctx.check(rc, "shifted_cocg_solve")
-    return SolveResult(G, iters, resid, status, rc, int(stats[0]), int(stats[1]), int(stats[2]))
+    return SolveResult(G, iters, resid, status, rc, int(stats[0]), int(stats[1]), int(stats[2]), int(stats[3]))
 
 
 def _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, stream, stats, ctas_per_sm=0):
@@ -287,7 +288,7 @@ def _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_m
 
 
 PROFILE_KERNELS = ("A_outer_H_product", "B_update", "IC_A_inner_S_product", "IC_B_inner_update", "C_rho",
-                   "R_refine")
+                   "R_refine", "R_refine_fp32")
 
 
 def profile(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_rows, *, reps=20,
@@ -345,7 +346,7 @@ def solve_local(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, sub_ptr, su
     iters = _empty((n_rhs,), np.int32, like)
     resid = _empty((n_rhs, n_z), np.float64, like)
     status = _empty((n_rhs,), np.int32, like)
-    stats = np.zeros(3, np.int64)
+    stats = np.zeros(4, np.int64)
     opts = _opts(ctx, tol, max_iter, precision, 0, seed_shift, inner_tol, inner_max, _stream_of(like), stats)
     Hc = H.c_struct()
     Sc = S.c_struct() if S is not None else None

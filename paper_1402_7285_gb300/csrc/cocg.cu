@@ -87,7 +87,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
              TB_ERR_ARG, "panel_w must be 0, 8, 16, 32 or 64");
     TB_CHECK(ctx, opts.seed_shift >= -1 && opts.seed_shift < n_z, TB_ERR_ARG, "seed_shift out of range");
     TB_CHECK(ctx, !profiling || (ms && n_rhs > 0), TB_ERR_ARG, "profile needs right-hand sides and ms[]");
-    if (opts.stats) opts.stats[0] = opts.stats[1] = opts.stats[2] = 0;
+    if (opts.stats) opts.stats[0] = opts.stats[1] = opts.stats[2] = opts.stats[3] = 0;
     if (n_rhs == 0) return TB_OK;
     cudaStream_t stream = (cudaStream_t)opts.stream;
     const bool mixed = opts.precision == TB_PREC_MIXED;
@@ -204,7 +204,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const size_t o_crow = take(sizeof(int64_t) * n_rhs);
     const size_t o_cptr = take(sizeof(int64_t) * (n_rhs + 1));
     const size_t o_erow = take(sizeof(int64_t) * std::max<int64_t>(n_out, 1));
-    const size_t o_stats = take(sizeof(int64_t) * 3);
+    const size_t o_stats = take(sizeof(int64_t) * 4);
     const size_t vsz = mixed ? sizeof(float) : sizeof(double);
     const size_t o_h32 = lowp ? take(vsz * H->nnzb * bb) : 0;
     const size_t o_s32 = (lowp && has_s) ? take(vsz * S->nnzb * bb) : 0;
@@ -219,7 +219,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     if (rc) return rc;
 
     TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_ctl, 0, sizeof(Ctrl), stream));
-    TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_stats, 0, sizeof(int64_t) * 3, stream));
+    TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_stats, 0, sizeof(int64_t) * 4, stream));
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_crow, h_rhs.data(), sizeof(int64_t) * n_rhs, cudaMemcpyHostToDevice, stream));
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(sb + o_cptr, h_optr.data(), sizeof(int64_t) * (n_rhs + 1), cudaMemcpyHostToDevice, stream));
     if (n_out > 0)
@@ -322,7 +322,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     TB_CUDA_TRY(ctx, cudaGetLastError());
     if (profiling) return TB_OK;
     if (opts.stats) {
-        TB_CUDA_TRY(ctx, cudaMemcpy(opts.stats, sb + o_stats, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost));
+        TB_CUDA_TRY(ctx, cudaMemcpy(opts.stats, sb + o_stats, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost));
     }
     std::vector<int32_t> stv(n_rhs);
     TB_CUDA_TRY(ctx, cudaMemcpy(stv.data(), d_status, sizeof(int32_t) * n_rhs, cudaMemcpyDeviceToHost));

@@ -84,6 +84,7 @@ __global__ void k_init_state(Panel<T> p, int has_s) {
         p.ctl->next_col = p.n_cols < W ? p.n_cols : W;
         p.ctl->inner_total = 0;
         p.ctl->refine_total = 0;
+        p.ctl->light_total = 0;
         p.ctl->refine_now = 0;
     }
 }
@@ -127,6 +128,11 @@ __global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
 // spreads the (pair, kept row) updates over all threads of the CTA, so the
 // kept rows of a column are updated in parallel, not one after another.
 constexpr int PAIR_CHUNK = 128;
+
+// A refinement pass takes S c in FP32 when every refining column's residual is
+// below REFINE_LIGHT times its inner tolerance target: the FP32 product's error
+// (about 1e-6 of the correction) then stays below inner_tol ||rt|| / 20.
+constexpr double REFINE_LIGHT = 5e4;
 
 // Resident CTAs per SM that IC_A and C are compiled for: four for df
 // panels with block edges <= 4 (64 registers suffice), otherwise the three of
@@ -801,8 +807,20 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
         const int cont = (!all_done) && (p.ctl->in_ctr < p.inner_max);
         if (p.ir) {
             // an FP32 sweep of the refinement: when it ends, the refinement kernel
-            // that follows in the loop body applies it (the loop condition is its)
-            if (!cont) p.ctl->refine_now = 1;
+            // that follows in the loop body applies it (the loop condition is its).
+            // When every refining column's correction is small (its residual below
+            // REFINE_LIGHT inner_tol ||rt||), the pass takes S c in FP32
+            // (refine_now = 2); otherwise in df (refine_now = 1).
+            if (!cont) {
+                int light = 1;
+                for (int c = 0; c < W; ++c) {
+                    const ColState &C = p.col[c];
+                    if (C.done || !C.in_sweep) continue;
+                    const double lim = REFINE_LIGHT * p.inner_tol;
+                    if (!(C.in_t2 <= lim * lim * C.rn2)) light = 0;
+                }
+                p.ctl->refine_now = light ? 2 : 1;
+            }
         } else if (p.in_graph) {
             cudaGraphSetConditional(p.h_inner, cont ? 1u : 0u);
         }
@@ -821,7 +839,8 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_inner_b(Panel<T> p) {
 template <typename T, int B, int W>
 __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_refine(Panel<T> p) {
     if constexpr (std::is_same<T, df>::value) {
-        if (!p.ctl->refine_now) return;
+        const int mode = p.ctl->refine_now; // 0: the sweep goes on; 1: df product; 2: FP32 product
+        if (!mode) return;
         using TM = Teams<df, W, NT>;
         const int team = threadIdx.x / TM::TPR, lane = threadIdx.x % TM::TPR;
         df *Y = p.R[(p.ctl->n + 1) & 1];
@@ -835,7 +854,36 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_refine(Panel<T> p) {
         const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
         for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
             cpx<df> sc[B][1];
-            bsr_row_product<df, B, float>(p.s_rp, p.s_ci, p.s_val, br, ld, sc, p.s_unit ? br : -1);
+            if (mode == 1) {
+                bsr_row_product<df, B, float>(p.s_rp, p.s_ci, p.s_val, br, ld, sc, p.s_unit ? br : -1);
+            } else { // a small correction: FP32 values of S, FP32 accumulation
+                float sr[B], si[B];
+#pragma unroll
+                for (int i = 0; i < B; ++i) sr[i] = si[i] = 0.f;
+                const int64_t k1 = p.s_rp[br + 1];
+                for (int64_t k = p.s_rp[br]; k < k1; ++k) {
+                    const int64_t col = p.s_ci[k];
+                    cpx<float> x[B][1];
+#pragma unroll
+                    for (int j = 0; j < B; ++j) ld(col * B + j, x[j]);
+                    if (p.s_unit && col == br) {
+#pragma unroll
+                        for (int i = 0; i < B; ++i) sr[i] += x[i][0].re, si[i] += x[i][0].im;
+                    } else {
+                        float a[B * B];
+                        ld_block<float, B>(p.s_val32 + k * (B * B), a);
+#pragma unroll
+                        for (int i = 0; i < B; ++i)
+#pragma unroll
+                            for (int j = 0; j < B; ++j) {
+                                sr[i] = fmaf(a[i * B + j], x[j][0].re, sr[i]);
+                                si[i] = fmaf(a[i * B + j], x[j][0].im, si[i]);
+                            }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < B; ++i) sc[i][0] = mk(df(sr[i]), df(si[i]));
+            }
 #pragma unroll
             for (int i = 0; i < B; ++i) {
                 const int64_t row = br * B + i;
@@ -889,6 +937,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_refine(Panel<T> p) {
             p.ctl->in_ctr = 0;
             p.ctl->refine_now = 0;
             p.ctl->refine_total += 1;
+            p.ctl->light_total += (mode == 2);
             if (p.in_graph) cudaGraphSetConditional(p.h_inner, any ? 1u : 0u);
         }
     }
@@ -962,6 +1011,7 @@ __global__ void k_writeout(Panel<T> p) {
         p.stats[0] = p.ctl->iter_ctr;
         p.stats[1] = p.ctl->inner_total;
         p.stats[2] = p.ctl->refine_total;
+        p.stats[3] = p.ctl->light_total;
     }
 }
 
@@ -1077,9 +1127,10 @@ struct SolveLaunch {
                 if (ir) return (void)k_inner_b<float, B, W><<<grid_f, block, 0, stream>>>(pf);
             k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
         };
-        // a refinement pass with its work done (outside the graph nothing sets refine_now)
-        auto refine = [&]() {
-            cudaMemsetAsync(&p.ctl->refine_now, 1, 1, stream);
+        // a refinement pass with its work done (outside the graph nothing sets
+        // refine_now): mode 1 takes S c in df, mode 2 in FP32
+        auto refine = [&](int mode) {
+            cudaMemsetAsync(&p.ctl->refine_now, mode, 1, stream);
             k_refine<T, B, W><<<grid, block, 0, stream>>>(p);
         };
         k_init_state<T, W><<<1, NT, 0, stream>>>(p, has_s_i);
@@ -1088,13 +1139,14 @@ struct SolveLaunch {
             k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
             inner_a();
             inner_b();
-            if (ir) refine();
+            if (ir) refine(1);
             k_rho<T, B, W><<<grid_a, block, 0, stream>>>(p, 1);
         }
         // events: [0] A [1] B [2] (untimed first inner pair) [3] IC_A [4] IC_B [5] R [6] C [7]
-        cudaEvent_t ev[8];
+        //         R in FP32 between [8] and [9]
+        cudaEvent_t ev[10];
         for (auto &e : ev) cudaEventCreate(&e);
-        double acc[6] = {0, 0, 0, 0, 0, 0};
+        double acc[7] = {0, 0, 0, 0, 0, 0, 0};
         for (int r = 0; r < profile_reps && !rc; ++r) {
             cudaEventRecord(ev[0], stream);
             if (has_s)
@@ -1118,11 +1170,17 @@ struct SolveLaunch {
                 cudaEventRecord(ev[4], stream);
                 inner_b();
                 cudaEventRecord(ev[5], stream);
-                if (ir) refine();
+                if (ir) refine(1);
                 cudaEventRecord(ev[6], stream);
                 k_rho<T, B, W><<<grid_a, block, 0, stream>>>(p, 0);
                 cudaEventRecord(ev[7], stream);
                 last = 7;
+                if (ir) {
+                    cudaEventRecord(ev[8], stream);
+                    refine(2);
+                    cudaEventRecord(ev[9], stream);
+                    last = 9;
+                }
             }
             cudaError_t e = cudaEventSynchronize(ev[last]);
             if (e != cudaSuccess) {
@@ -1130,8 +1188,8 @@ struct SolveLaunch {
                 break;
             }
             // (kernel slot, start event, end event)
-            const int spans[6][3] = {{0, 0, 1}, {1, 1, 2}, {2, 3, 4}, {3, 4, 5}, {4, 6, 7}, {5, 5, 6}};
-            for (int q = 0; q < (has_s ? 6 : 2); ++q) {
+            const int spans[7][3] = {{0, 0, 1}, {1, 1, 2}, {2, 3, 4}, {3, 4, 5}, {4, 6, 7}, {5, 5, 6}, {6, 8, 9}};
+            for (int q = 0; q < (has_s ? (ir ? 7 : 6) : 2); ++q) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, ev[spans[q][1]], ev[spans[q][2]]);
                 acc[spans[q][0]] += ms;
@@ -1139,9 +1197,9 @@ struct SolveLaunch {
         }
         for (auto &e : ev) cudaEventDestroy(e);
         for (int k = 0; k < 8; ++k) ms_out[k] = 0.0;
-        for (int k = 0; k < 6; ++k) ms_out[k] = acc[k] / profile_reps;
+        for (int k = 0; k < 7; ++k) ms_out[k] = acc[k] / profile_reps;
         if (!has_s) ms_out[2] = ms_out[3] = ms_out[4] = 0.0;
-        if (!ir) ms_out[5] = 0.0;
+        if (!ir) ms_out[5] = ms_out[6] = 0.0;
     }
 
     template <typename T, int B, int W>

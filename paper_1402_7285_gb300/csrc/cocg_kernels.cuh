@@ -84,7 +84,8 @@ struct Ctrl {
     int64_t refine_total; // refinement passes (df panels) summed over the panel
     int32_t refine_now;   // set by the last FP32 sweep step: the next refinement kernel does its work
     int32_t pad32;
-    int64_t pad[2];
+    int64_t light_total;  // of those, passes that took S c in FP32
+    int64_t pad[1];
 };
 
 // Vectors of the inner CG on S that only steer it: its search direction d and
@@ -155,7 +156,7 @@ struct Panel {
     int32_t *iters;
     double *resid;
     int32_t *status;
-    int64_t *stats;  // [3] = (outer iterations, inner iterations, refinements)
+    int64_t *stats;  // [4] = (outer iterations, inner iterations, refinements, FP32 refinements)
 };
 
 // ---------------------------------------------------------------- accumulators
