@@ -69,7 +69,7 @@ int tb_ctx_destroy(tb_ctx *ctx);
 const char *tb_status_string(int status);
 /* The message of the last failure recorded in ctx (never NULL). */
 const char *tb_last_error(const tb_ctx *ctx);
-/* Library version, e.g. 10000 for 1.0.0. */
+/* Library version, e.g. 10100 for 1.1.0. */
 int tb_version(void);
 
 /* ------------------------------------------------------ system builder */
@@ -192,11 +192,26 @@ typedef struct {
                             with df panels and block edges <= 4 the inner S
                             product and the rho kernel run one more (at most 4) */
     void *stream;        /* cudaStream_t to queue work on                         */
+    int32_t solver;      /* TB_SOLVER_COCG (default) or TB_SOLVER_QMR                */
     int64_t *stats;      /* optional host array [4]: outer iterations, inner
                             iterations, and (DF64 with S) refinement passes and
                             of those the ones that took S c in FP32 (written
                             before returning)                                     */
 } tb_solve_opts;
+
+/* Solvers of Sec. 3 for Eq. 2:
+ * TB_SOLVER_COCG  generalized shifted COCG: each shift stops when its residual
+ *                 ||rt|| / |pi^m| <= tol (resid is that residual);
+ * TB_SOLVER_QMR   generalized shifted QMR: the quasi-minimal residual iterates
+ *                 of the same Krylov space, obtained from the COCG iterates by
+ *                 QMR smoothing (1/tau_n^2 = 1/tau_{n-1}^2 + 1/omega_n^2,
+ *                 xq_n = xq_{n-1} + (tau_n / omega_n)^2 (x_n - xq_{n-1}), omega_n =
+ *                 sqrt|r_n^T S r_n| / |pi^m_n|, the quasi-norm of the shift's COCG
+ *                 residual; equal in exact arithmetic to QMR on the unconjugated
+ *                 Lanczos process); a shift stops when its quasi-residual
+ *                 tau_n / tau_0 <= tol (resid is that ratio).  No df64 restarts. */
+#define TB_SOLVER_COCG 0
+#define TB_SOLVER_QMR 1
 
 /* Fill `opts` with the defaults above. */
 void tb_solve_opts_default(tb_solve_opts *opts);

@@ -23,15 +23,15 @@ import numpy as np
 
 from . import _lib
 from ._lib import (TB_COL_BREAKDOWN, TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_NONFINITE, TB_ERR_ARG,
-                   TB_ERR_SIZE, TB_ERR_STRUCTURE, TB_PREC_DF64, TB_PREC_FP64, TB_PREC_MIXED, TB_WARN_BREAKDOWN,
-                   TB_WARN_MAX_ITER, TB_WARN_NONFINITE)
+                   TB_ERR_SIZE, TB_ERR_STRUCTURE, TB_ERR_UNSUPPORTED, TB_PREC_DF64, TB_PREC_FP64, TB_PREC_MIXED, TB_SOLVER_COCG,
+                   TB_SOLVER_QMR, TB_WARN_BREAKDOWN, TB_WARN_MAX_ITER, TB_WARN_NONFINITE)
 
 __all__ = ["Context", "Bsr", "TbError", "build_system", "bsr_spmm", "spmm_profile", "solve", "profile", "reduce_ldos_dm",
            "spec_to_c", "local_subspaces", "solve_local", "descriptors", "mlp_grad", "mlp_train", "mlp_predict",
            "mlp_param_count",
            "TB_PREC_FP64", "TB_PREC_MIXED", "TB_PREC_DF64", "TB_COL_CONVERGED", "TB_COL_MAX_ITER", "TB_COL_BREAKDOWN",
            "TB_COL_NONFINITE", "TB_WARN_MAX_ITER", "TB_WARN_BREAKDOWN", "TB_WARN_NONFINITE", "TB_ERR_ARG",
-           "TB_ERR_SIZE", "TB_ERR_STRUCTURE"]
+           "TB_ERR_SIZE", "TB_ERR_STRUCTURE", "TB_ERR_UNSUPPORTED", "TB_SOLVER_COCG", "TB_SOLVER_QMR"]
 
 
 class TbError(RuntimeError):
@@ -250,8 +250,9 @@ class SolveResult:
 
 def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_rows, *, tol=1e-10,
           max_iter=100000, precision=TB_PREC_FP64, panel_w=0, seed_shift=-1, inner_tol=0.0, inner_max=0,
-          outputs_like=None, ctas_per_sm=0) -> SolveResult:
-    """G[(out_row_ptr[c] + k), m] = e_i^T (z_m S - H)^{-1} e_j, i = out_rows[...], j = rhs_rows[c]."""
+          outputs_like=None, ctas_per_sm=0, solver=TB_SOLVER_COCG) -> SolveResult:
+    """G[(out_row_ptr[c] + k), m] = e_i^T (z_m S - H)^{-1} e_j, i = out_rows[...], j = rhs_rows[c]
+    (solver: TB_SOLVER_COCG or TB_SOLVER_QMR)."""
     like = H.val if outputs_like is None else outputs_like
     zc = _as(z, np.complex128, like=like)
     rhs = _as(rhs_rows, np.int64, like=like)
@@ -266,7 +267,7 @@ def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_
     status = _empty((n_rhs,), np.int32, like)
     stats = np.zeros(4, np.int64)
     opts = _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, _stream_of(like), stats,
-                 ctas_per_sm)
+                 ctas_per_sm, solver)
     Hc = H.c_struct()
     Sc = S.c_struct() if S is not None else None
     rc = ctx.lib.shifted_cocg_solve(ctx.h, ctypes.byref(Hc), ctypes.byref(Sc) if Sc is not None else None,
@@ -276,10 +277,12 @@ def solve(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, out_row_ptr, out_
     return SolveResult(G, iters, resid, status, rc, int(stats[0]), int(stats[1]), int(stats[2]), int(stats[3]))
 
 
-def _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, stream, stats, ctas_per_sm=0):
+def _opts(ctx, tol, max_iter, precision, panel_w, seed_shift, inner_tol, inner_max, stream, stats, ctas_per_sm=0,
+          solver=TB_SOLVER_COCG):
     opts = _lib.TbSolveOpts()
     ctx.lib.tb_solve_opts_default(ctypes.byref(opts))
     opts.ctas_per_sm = ctas_per_sm
+    opts.solver = solver
     opts.tol, opts.max_iter, opts.precision, opts.panel_w = tol, max_iter, precision, panel_w
     opts.seed_shift, opts.inner_tol, opts.inner_max = seed_shift, inner_tol, inner_max
     opts.stream = stream
@@ -331,7 +334,7 @@ def local_subspaces(H: Bsr, rhs_rows, radii):
 
 def solve_local(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, sub_ptr, sub_atoms, out_row_ptr, out_rows,
                 *, order=None, tol=1e-10, max_iter=100000, precision=TB_PREC_FP64, seed_shift=-1, inner_tol=0.0,
-                inner_max=0) -> SolveResult:
+                inner_max=0, solver=TB_SOLVER_COCG) -> SolveResult:
     """Truncated-subspace solves, one CTA per column (shifted_cocg_solve_local)."""
     like = H.val
     zc = _as(z, np.complex128, like=like)
@@ -347,7 +350,8 @@ def solve_local(ctx: Context, H: Bsr, S: Optional[Bsr], z, rhs_rows, sub_ptr, su
     resid = _empty((n_rhs, n_z), np.float64, like)
     status = _empty((n_rhs,), np.int32, like)
     stats = np.zeros(4, np.int64)
-    opts = _opts(ctx, tol, max_iter, precision, 0, seed_shift, inner_tol, inner_max, _stream_of(like), stats)
+    opts = _opts(ctx, tol, max_iter, precision, 0, seed_shift, inner_tol, inner_max, _stream_of(like), stats,
+                 solver=solver)
     Hc = H.c_struct()
     Sc = S.c_struct() if S is not None else None
     rc = ctx.lib.shifted_cocg_solve_local(ctx.h, ctypes.byref(Hc), ctypes.byref(Sc) if Sc is not None else None,

@@ -12,6 +12,7 @@ TB_ERR_ARG, TB_ERR_CUDA, TB_ERR_ALLOC, TB_ERR_UNSUPPORTED, TB_ERR_SIZE, TB_ERR_S
 TB_WARN_MAX_ITER, TB_WARN_BREAKDOWN, TB_WARN_NONFINITE = 1, 2, 4
 TB_COL_CONVERGED, TB_COL_MAX_ITER, TB_COL_BREAKDOWN, TB_COL_NONFINITE = 0, 1, 2, 3
 TB_PREC_FP64, TB_PREC_MIXED, TB_PREC_DF64 = 0, 1, 2
+TB_SOLVER_COCG, TB_SOLVER_QMR = 0, 1
 TB_LATTICE_SC_PERIODIC, TB_LATTICE_FCC_CLUSTER = 0, 1
 TB_ONSITE_UNIFORM, TB_ONSITE_DIAG_NORMAL = 0, 1
 TB_HOP_CONST, TB_HOP_NORMAL = 0, 1
@@ -44,7 +45,7 @@ class TbSolveOpts(ctypes.Structure):
         ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("panel_w", ctypes.c_int32), ("seed_shift", ctypes.c_int32), ("inner_tol", ctypes.c_double),
         ("inner_max", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("stream", ctypes.c_void_p),
-        ("stats", ctypes.c_void_p),
+        ("solver", ctypes.c_int32), ("stats", ctypes.c_void_p),
     ]
 
 

@@ -86,6 +86,7 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
                       opts.panel_w == 64,
              TB_ERR_ARG, "panel_w must be 0, 8, 16, 32 or 64");
     TB_CHECK(ctx, opts.seed_shift >= -1 && opts.seed_shift < n_z, TB_ERR_ARG, "seed_shift out of range");
+    TB_CHECK(ctx, opts.solver == TB_SOLVER_COCG || opts.solver == TB_SOLVER_QMR, TB_ERR_ARG, "bad solver");
     TB_CHECK(ctx, !profiling || (ms && n_rhs > 0), TB_ERR_ARG, "profile needs right-hand sides and ms[]");
     if (opts.stats) opts.stats[0] = opts.stats[1] = opts.stats[2] = opts.stats[3] = 0;
     if (n_rhs == 0) return TB_OK;
@@ -215,7 +216,8 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     char *sb = (char *)small_base;
     void *proj_base = nullptr;
     const int64_t proj_entries = (int64_t)W * max_col_ent * n_z; // one region of max_col_ent rows per slot
-    rc = ws_get(ctx, WS_SOLVE_PROJ, sizeof(c64) * 2 * proj_entries, &proj_base);
+    const bool qmr = opts.solver == TB_SOLVER_QMR;
+    rc = ws_get(ctx, WS_SOLVE_PROJ, sizeof(c64) * (qmr ? 3 : 2) * proj_entries, &proj_base);
     if (rc) return rc;
 
     TB_CUDA_TRY(ctx, cudaMemsetAsync(sb + o_ctl, 0, sizeof(Ctrl), stream));
@@ -283,6 +285,8 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.max_col_ent = (int32_t)max_col_ent;
     p.xs = (c64 *)proj_base;
     p.ps = (c64 *)proj_base + proj_entries;
+    p.xq = qmr ? (c64 *)proj_base + 2 * proj_entries : nullptr;
+    p.qmr = qmr ? 1 : 0;
     p.col_row = (const int64_t *)(sb + o_crow);
     p.col_ptr = (const int64_t *)(sb + o_cptr);
     p.ent_row = (const int64_t *)(sb + o_erow);
@@ -290,7 +294,8 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.part = sb + o_part;
     p.ctl = (Ctrl *)(sb + o_ctl);
     p.tol = opts.tol;
-    p.stall2 = opts.precision == TB_PREC_DF64 ? 1e-20 : 0.0; // df64 restarts (see k_outer)
+    // df64 restarts (see k_outer); not with gsQMR, whose smoothing runs over one seed's iterates
+    p.stall2 = (opts.precision == TB_PREC_DF64 && !qmr) ? 1e-20 : 0.0;
     // inner tolerance: FP64 and FP32 panels 1e-3 tol (floors 1e-13, 1e-7); df panels
     // refine to 1e-5 tol (floor 1e-12): the refinement makes the tighter target cheap,
     // and inexact inner solves are what separates the shifted results from the FP64 ones

@@ -53,6 +53,7 @@ __device__ __forceinline__ ShiftState fresh_shift() {
     S.resid = 1.0;
     S.active = 1;
     S.conv_it = -1;
+    S.qinv = S.qinv0 = 0.0;
     return S;
 }
 
@@ -118,6 +119,7 @@ __global__ void k_init_vec(Panel<T> p, int64_t n_rows, int has_s) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ne; t += stride) {
         p.xs[t] = mk(0.0, 0.0);
         p.ps[t] = mk(0.0, 0.0);
+        if (p.xq) p.xq[t] = mk(0.0, 0.0);
     }
 }
 
@@ -143,9 +145,16 @@ constexpr int ctas_light() {
 }
 
 // A(n): rotate pi, test ||rt_n|| / |pi_n| <= tol, then p^m_n = r_n / pi_n + beta^m_{n-1} p^m_{n-1}.
+// gsQMR: the QMR iterate is the COCG one smoothed (Zhou & Walker's QMR smoothing,
+// equal in exact arithmetic to QMR on the complex-symmetric Lanczos process of
+// the same Krylov space): with omega_n = sqrt|rho_n| / |pi_n| the quasi-norm of
+// the shift's COCG residual (rho_n = r_n^T S r_n), 1/tau_n^2 = 1/tau_{n-1}^2 +
+// 1/omega_n^2 and xq_n = xq_{n-1} + (tau_n^2 / omega_n^2)(x_n - xq_{n-1}); the shift
+// stops when tau_n / tau_0 <= tol.
 template <typename T, int W>
 __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) {
     __shared__ c64 s_a[PAIR_CHUNK], s_b[PAIR_CHUNK];
+    __shared__ double s_eta[PAIR_CHUNK];
     __shared__ int s_c[PAIR_CHUNK], s_m[PAIR_CHUNK], s_on[PAIR_CHUNK];
     const int P = W * p.nz;
     const int q0 = (int)((int64_t)blockIdx.x * P / gridDim.x), q1 = (int)((int64_t)(blockIdx.x + 1) * P / gridDim.x);
@@ -160,7 +169,17 @@ __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) 
             if (!C.done && S.active) {
                 S.pi_prev = S.pi;
                 S.pi = S.pi_next;
-                const double res = sqrt(C.rn2) / sqrt(cabs2(S.pi));
+                double res;
+                if (p.qmr) {
+                    const double w2inv = cabs2(S.pi) / sqrt(cabs2(C.rho)); // 1 / omega_n^2
+                    if (S.qinv == 0.0) S.qinv0 = w2inv;
+                    S.qinv += w2inv;
+                    s_eta[t] = w2inv / S.qinv;
+                    res = sqrt(S.qinv0 / S.qinv);
+                    on = 2; // smoothing update of the kept rows
+                } else {
+                    res = sqrt(C.rn2) / sqrt(cabs2(S.pi));
+                }
                 S.resid = res;
                 if (res <= p.tol) {
                     S.active = 0;
@@ -170,7 +189,7 @@ __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) 
                     const c64 ratio = cdiv(S.pi_prev, S.pi);
                     s_b[t] = (ratio * ratio) * C.beta_prev;
                     s_a[t] = cdiv(mk(1.0, 0.0), S.pi);
-                    on = 1;
+                    on |= 1;
                 }
             }
             s_on[t] = on;
@@ -184,11 +203,13 @@ __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) 
             const int c = s_c[t], m = s_m[t];
             const ColState &C = p.col[c];
             if (k >= C.n_ent) continue;
+            const int64_t e = ((int64_t)c * KM + k) * p.nz + m;
+            if (s_on[t] & 2) p.xq[e] = p.xq[e] + s_eta[t] * (p.xs[e] - p.xq[e]);
+            if (!(s_on[t] & 1)) continue;
             const int64_t row = p.ent_row[C.ent0 + k];
             const T *rp = Rc + (row * W + c) * 2;
             const c64 rv = mk((double)rp[0], (double)rp[1]);
-            c64 *ps = p.ps + ((int64_t)c * KM + k) * p.nz + m;
-            *ps = s_a[t] * rv + s_b[t] * (*ps);
+            p.ps[e] = s_a[t] * rv + s_b[t] * p.ps[e];
         }
         __syncthreads();
     }
@@ -372,7 +393,8 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
         for (int f = 0; f < n_fin; ++f) {
             const ColState &C = p.col[fin[f]];
             const int64_t base = (int64_t)fin[f] * KM * p.nz, ne = (int64_t)C.n_ent * p.nz;
-            for (int64_t t = threadIdx.x; t < ne; t += NT) p.G[C.ent0 * p.nz + t] = p.xs[base + t];
+            const c64 *xo = p.qmr ? p.xq : p.xs;
+            for (int64_t t = threadIdx.x; t < ne; t += NT) p.G[C.ent0 * p.nz + t] = xo[base + t];
             for (int m = threadIdx.x; m < p.nz; m += NT)
                 p.resid[C.dst * p.nz + m] = p.sh[(int64_t)fin[f] * p.nz + m].resid;
         }
@@ -402,6 +424,7 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
             for (int64_t t = threadIdx.x; t < (int64_t)KM * p.nz; t += NT) {
                 p.xs[base + t] = mk(0.0, 0.0);
                 p.ps[base + t] = mk(0.0, 0.0);
+                if (p.xq) p.xq[base + t] = mk(0.0, 0.0);
             }
         }
         __syncthreads();
@@ -994,7 +1017,7 @@ __global__ void k_writeout(Panel<T> p) {
         const ColState &C = p.col[t / per_slot];
         const int64_t r = t % per_slot;
         if (C.dst < 0 || r >= (int64_t)C.n_ent * p.nz) continue;
-        p.G[C.ent0 * p.nz + r] = p.xs[t];
+        p.G[C.ent0 * p.nz + r] = p.qmr ? p.xq[t] : p.xs[t];
     }
     for (int64_t q = tid; q < (int64_t)W * p.nz; q += stride) {
         const int64_t dst = p.col[q / p.nz].dst;

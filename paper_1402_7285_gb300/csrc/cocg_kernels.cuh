@@ -68,6 +68,10 @@ struct ShiftState {
     c64 alpha_s;
     double resid;
     int32_t active, conv_it;
+    // QMR smoothing (gsQMR): sum over the iterates so far of 1 / omega_k^2, omega_k
+    // the quasi-norm sqrt|rho_k| / |pi_k| of the shift's COCG residual, and its
+    // first term (the quasi-residual of the zero start)
+    double qinv, qinv0;
 };
 
 struct Ctrl {
@@ -134,6 +138,8 @@ struct Panel {
     const c64 *z;    // [nz]
     // kept rows (projection entries): a region of max_col_ent entries per slot
     c64 *xs, *ps;    // [W][max_col_ent][nz]
+    c64 *xq;         // gsQMR: the QMR-smoothed iterates, same layout (null for gsCOCG)
+    int32_t qmr;     // 1: gsQMR (results and stopping test from the smoothed iterates)
     // the column queue (device): columns are loaded into slots in this order
     const int64_t *col_row;     // [n_cols]   right-hand side row j of each column
     const int64_t *col_ptr;     // [n_cols+1] kept-row offsets (rows of G) of each column

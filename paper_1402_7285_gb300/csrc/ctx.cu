@@ -184,7 +184,7 @@ const char *tb_status_string(int status) {
 
 const char *tb_last_error(const tb_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
 
-int tb_version(void) { return 10000; }
+int tb_version(void) { return 10100; }
 
 void tb_solve_opts_default(tb_solve_opts *o) {
     if (!o) return;

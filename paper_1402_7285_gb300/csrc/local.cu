@@ -57,6 +57,7 @@ extern "C" int shifted_cocg_solve_local(tb_ctx *ctx, const tb_bsr *H, const tb_b
              TB_ERR_ARG, "bad precision");
     TB_CHECK(ctx, opts.tol > 0.0 && opts.max_iter >= 0, TB_ERR_ARG, "tol must be > 0 and max_iter >= 0");
     if (opts.stats) opts.stats[0] = opts.stats[1] = opts.stats[2] = opts.stats[3] = 0;
+    TB_CHECK(ctx, opts.solver == TB_SOLVER_COCG, TB_ERR_UNSUPPORTED, "the local solver runs gsCOCG only");
     if (n_rhs == 0) return TB_OK;
     cudaStream_t stream = (cudaStream_t)opts.stream;
     const bool mixed = opts.precision == TB_PREC_MIXED;
