@@ -349,6 +349,27 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         ctx.close()
         return {"kernel_profile": prof}
+    if args.full_vector:
+        # every row kept: the shifted solutions x^m and directions p^m as full vectors
+        # (W columns x M rows x n_z shifts, FP64 complex); A updates p^m (read, write),
+        # B' updates x^m (read, write) and reads p^m: 5 W M n_z 16 bytes per iteration
+        cols, ptr, orows = dev_panel(0)
+        M = Hh.n_rows
+        full_rows = torch.arange(M, device=dev, dtype=torch.int64).repeat(W)
+        full_ptr = torch.arange(W + 1, device=dev, dtype=torch.int64) * M
+        base = tb.profile(ctx, H, S, zt, cols, ptr, orows, reps=args.profile_reps, precision=prec, panel_w=W)
+        full = tb.profile(ctx, H, S, zt, cols, full_ptr, full_rows, reps=args.profile_reps, precision=prec,
+                          panel_w=W)
+        torch.cuda.synchronize()
+        ctx.close()
+        extra = (full["A_outer_H_product"] + full["B_update"]) - (base["A_outer_H_product"] + base["B_update"])
+        nbytes = 5 * W * M * n_z * 16
+        return {"full_vector": {"kept_rows_per_column": M, "projection_bytes": 2 * W * M * n_z * 16,
+                                "ms_A_B_block_pattern": base["A_outer_H_product"] + base["B_update"],
+                                "ms_A_B_full_vectors": full["A_outer_H_product"] + full["B_update"],
+                                "pair_step_bytes_per_iteration": nbytes, "pair_step_ms": extra,
+                                "pair_step_gbs": nbytes / (extra * 1e-3) / 1e9,
+                                "frac_of_hbm": nbytes / (extra * 1e-3) / 1e9 / measured_peaks()["hbm_gbs"]}}
 
     def step_device(cols, ptr, orows):
         r = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=prec, panel_w=W,
@@ -650,6 +671,8 @@ def main():
     ap.add_argument("--kernel-profile", action="store_true",
                     help="only launch the solver kernels of one panel (CUDA events; for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=100000)
+    ap.add_argument("--full-vector", action="store_true",
+                    help="only time the shifted steps with every row kept (full-vector shifted solutions)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--spmm-only", action="store_true",
                     help="only the SpMM bandwidth figure (the product kernel alone, C2's H)")
@@ -713,7 +736,7 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, rank, world)
-    if "kernel_profile" in out:
+    if "kernel_profile" in out or "full_vector" in out:
         if rank == 0:
             print(json.dumps(out))
         return

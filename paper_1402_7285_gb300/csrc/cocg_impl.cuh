@@ -197,8 +197,10 @@ __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) 
             s_m[t] = m;
         }
         __syncthreads();
+        // pairs fastest: the pairs of a chunk are consecutive shifts of a column, so
+        // consecutive threads touch consecutive entries of a kept row (coalesced)
         for (int64_t i = threadIdx.x; i < (int64_t)np * KM; i += blockDim.x) {
-            const int t = (int)(i / KM), k = (int)(i % KM);
+            const int t = (int)(i % np), k = (int)(i / np);
             if (!s_on[t]) continue;
             const int c = s_c[t], m = s_m[t];
             const ColState &C = p.col[c];
@@ -252,8 +254,10 @@ __device__ void pair_step_B(const Panel<T> &p) {
             s_m[t] = m;
         }
         __syncthreads();
+        // pairs fastest: the pairs of a chunk are consecutive shifts of a column, so
+        // consecutive threads touch consecutive entries of a kept row (coalesced)
         for (int64_t i = threadIdx.x; i < (int64_t)np * KM; i += blockDim.x) {
-            const int t = (int)(i / KM), k = (int)(i % KM);
+            const int t = (int)(i % np), k = (int)(i / np);
             if (!s_on[t]) continue;
             const int c = s_c[t], m = s_m[t];
             if (k >= p.col[c].n_ent) continue;
