@@ -206,6 +206,13 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     const size_t o_cptr = take(sizeof(int64_t) * (n_rhs + 1));
     const size_t o_erow = take(sizeof(int64_t) * std::max<int64_t>(n_out, 1));
     const size_t o_stats = take(sizeof(int64_t) * 4);
+    // many kept rows: the shifted steps' kept-row updates run row-parallel (k_rows_A / k_rows_B)
+    const bool rowpar = max_col_ent >= 256;
+    const size_t o_coefa = rowpar ? take(sizeof(c64) * 2 * W * n_z) : 0;
+    const size_t o_coefb = rowpar ? take(sizeof(c64) * W * n_z) : 0;
+    const size_t o_eta = rowpar ? take(sizeof(double) * W * n_z) : 0;
+    const size_t o_flaga = rowpar ? take(sizeof(int32_t) * W * n_z) : 0;
+    const size_t o_flagb = rowpar ? take(sizeof(int32_t) * W * n_z) : 0;
     const size_t vsz = mixed ? sizeof(float) : sizeof(double);
     const size_t o_h32 = lowp ? take(vsz * H->nnzb * bb) : 0;
     const size_t o_s32 = (lowp && has_s) ? take(vsz * S->nnzb * bb) : 0;
@@ -287,6 +294,14 @@ int run_solver(tb_ctx *ctx, const tb_bsr *H, const tb_bsr *S, const double *z, i
     p.ps = (c64 *)proj_base + proj_entries;
     p.xq = qmr ? (c64 *)proj_base + 2 * proj_entries : nullptr;
     p.qmr = qmr ? 1 : 0;
+    if (rowpar) {
+        p.rowpar = 1;
+        p.coefA = (c64 *)(sb + o_coefa);
+        p.coefB = (c64 *)(sb + o_coefb);
+        p.etaA = (double *)(sb + o_eta);
+        p.flagA = (int32_t *)(sb + o_flaga);
+        p.flagB = (int32_t *)(sb + o_flagb);
+    }
     p.col_row = (const int64_t *)(sb + o_crow);
     p.col_ptr = (const int64_t *)(sb + o_cptr);
     p.ent_row = (const int64_t *)(sb + o_erow);

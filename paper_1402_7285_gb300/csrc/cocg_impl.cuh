@@ -195,8 +195,14 @@ __device__ void pair_step_A(const Panel<T> &p, const T *__restrict__ Rc, int n) 
             s_on[t] = on;
             s_c[t] = c;
             s_m[t] = m;
+            if (p.rowpar) { // k_rows_A applies them
+                p.flagA[q] = on;
+                if (on & 1) p.coefA[2 * q] = s_a[t], p.coefA[2 * q + 1] = s_b[t];
+                if (on & 2) p.etaA[q] = s_eta[t];
+            }
         }
         __syncthreads();
+        if (p.rowpar) continue;
         // pairs fastest: the pairs of a chunk are consecutive shifts of a column, so
         // consecutive threads touch consecutive entries of a kept row (coalesced)
         for (int64_t i = threadIdx.x; i < (int64_t)np * KM; i += blockDim.x) {
@@ -252,8 +258,13 @@ __device__ void pair_step_B(const Panel<T> &p) {
             s_on[t] = on;
             s_c[t] = c;
             s_m[t] = m;
+            if (p.rowpar) { // k_rows_B applies it
+                p.flagB[q] = on;
+                if (on) p.coefB[q] = s_a[t];
+            }
         }
         __syncthreads();
+        if (p.rowpar) continue;
         // pairs fastest: the pairs of a chunk are consecutive shifts of a column, so
         // consecutive threads touch consecutive entries of a kept row (coalesced)
         for (int64_t i = threadIdx.x; i < (int64_t)np * KM; i += blockDim.x) {
@@ -265,6 +276,68 @@ __device__ void pair_step_B(const Panel<T> &p) {
             p.xs[e] = p.xs[e] + s_a[t] * p.ps[e];
         }
         __syncthreads();
+    }
+}
+
+// ----------------------------------------------- row-parallel kept-row updates
+// With many kept rows per column (full-vector shifted solutions) the pair steps
+// only compute the per-pair coefficients; these kernels apply them to every
+// (column, kept row, shift), shifts fastest, so the FP64 complex arrays stream
+// at full width.  A column that restarts in this iteration (a stall restart or a
+// slot that took the next column) is skipped: A has already cleared its arrays.
+// k_rows_A (after A): p^m_n = r_n / pi_n + beta^m_{n-1} p^m_{n-1}; gsQMR smoothing.
+// Index of work item t: column c, kept row k, shift m (32-bit division when the
+// work fits, the common case).
+__device__ __forceinline__ void rows_index(int64_t t, int64_t per, int nz, bool small, int &c, int64_t &k, int &m) {
+    if (small) {
+        const uint32_t tt = (uint32_t)t, pp = (uint32_t)per, cc = tt / pp, r = tt - cc * pp, kk = r / (uint32_t)nz;
+        c = (int)cc, k = kk, m = (int)(r - kk * (uint32_t)nz);
+    } else {
+        c = (int)(t / per);
+        const int64_t r = t - (int64_t)c * per;
+        k = r / nz;
+        m = (int)(r - k * nz);
+    }
+}
+
+template <typename T, int W>
+__global__ void k_rows_A(Panel<T> p, int has_s) {
+    const int n = p.ctl->n;
+    const T *Rc = has_s ? p.R[n & 1] : p.RT;
+    const int64_t KM = p.max_col_ent, per = KM * p.nz;
+    const bool small = W * per < (int64_t)UINT32_MAX;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < W * per; t += stride) {
+        int c, m;
+        int64_t k;
+        rows_index(t, per, p.nz, small, c, k, m);
+        const ColState &C = p.col[c];
+        if (k >= C.n_ent || C.restart) continue;
+        const int64_t q = (int64_t)c * p.nz + m;
+        const int on = p.flagA[q];
+        if (!on) continue;
+        if (on & 2) p.xq[t] = p.xq[t] + p.etaA[q] * (p.xs[t] - p.xq[t]);
+        if (on & 1) {
+            const int64_t row = p.ent_row[C.ent0 + k];
+            const T *rp = Rc + (row * W + c) * 2;
+            p.ps[t] = p.coefA[2 * q] * mk((double)rp[0], (double)rp[1]) + p.coefA[2 * q + 1] * p.ps[t];
+        }
+    }
+}
+
+// k_rows_B (after B / B'): x^m += alpha^m_n p^m_n.
+template <typename T, int W>
+__global__ void k_rows_B(Panel<T> p) {
+    const int64_t KM = p.max_col_ent, per = KM * p.nz;
+    const bool small = W * per < (int64_t)UINT32_MAX;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < W * per; t += stride) {
+        int c, m;
+        int64_t k;
+        rows_index(t, per, p.nz, small, c, k, m);
+        if (k >= p.col[c].n_ent) continue;
+        const int64_t q = (int64_t)c * p.nz + m;
+        if (p.flagB[q]) p.xs[t] = p.xs[t] + p.coefB[q] * p.ps[t];
     }
 }
 
@@ -398,7 +471,14 @@ __global__ void __launch_bounds__(NT, (B <= 4 ? 3 : 1)) k_outer(Panel<T> p) {
             const ColState &C = p.col[fin[f]];
             const int64_t base = (int64_t)fin[f] * KM * p.nz, ne = (int64_t)C.n_ent * p.nz;
             const c64 *xo = p.qmr ? p.xq : p.xs;
-            for (int64_t t = threadIdx.x; t < ne; t += NT) p.G[C.ent0 * p.nz + t] = xo[base + t];
+            for (int64_t t = threadIdx.x; t < ne; t += NT) {
+                c64 v = xo[base + t];
+                if (p.rowpar && p.qmr) { // this iteration's smoothing step is still pending (k_rows_A)
+                    const int64_t q = (int64_t)fin[f] * p.nz + t % p.nz;
+                    if (p.flagA[q] & 2) v = v + p.etaA[q] * (p.xs[base + t] - v);
+                }
+                p.G[C.ent0 * p.nz + t] = v;
+            }
             for (int m = threadIdx.x; m < p.nz; m += NT)
                 p.resid[C.dst * p.nz + m] = p.sh[(int64_t)fin[f] * p.nz + m].resid;
         }
@@ -1106,6 +1186,12 @@ struct SolveLaunch {
     int vec_grid(int W) const {
         return (int)std::min<int64_t>(std::max<int64_t>((n_rows * W + NT - 1) / NT, 1), 152 * 8);
     }
+    // the row-parallel kept-row kernels: one thread per (column, kept row, shift)
+    template <typename T>
+    static int rows_grid(const Panel<T> &p, int W) {
+        const int64_t work = (int64_t)W * p.max_col_ent * p.nz;
+        return (int)std::min<int64_t>(std::max<int64_t>((work + NT - 1) / NT, 1), 152 * 8);
+    }
 
     template <typename T, int B, int W>
     void run() {
@@ -1180,11 +1266,13 @@ struct SolveLaunch {
                 k_outer<T, B, W, true><<<grid, block, 0, stream>>>(p);
             else
                 k_outer<T, B, W, false><<<grid, block, 0, stream>>>(p);
+            if (p.rowpar) k_rows_A<T, W><<<rows_grid(p, W), block, 0, stream>>>(p, has_s_i);
             cudaEventRecord(ev[1], stream);
             if (has_s)
                 k_update_S<T, B, W><<<grid, block, 0, stream>>>(p);
             else
                 k_update_sI<T, B, W><<<grid, block, 0, stream>>>(p);
+            if (p.rowpar) k_rows_B<T, W><<<rows_grid(p, W), block, 0, stream>>>(p);
             cudaEventRecord(ev[2], stream);
             int last = 2;
             if (has_s) {
@@ -1285,19 +1373,25 @@ struct SolveLaunch {
         void *a_body[] = {&p_body};
         void *a_fbody[] = {&pf_body};
         void *a_body_rho[] = {&p_body, &init0};
+        void *a_rows_a[] = {&p_body, &has_s_i};
+        const dim3 rgrid(rows_grid(p, W));
         if (!gb.rc) {
             if (has_s) {
                 p_body.h_inner = gb.handle(ob, 0u, 0u);
                 pf_body = fp32_view(p_body);
                 cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, true>, grid, block, a_body, nullptr, 0);
+                if (p.rowpar) x = gb.add_kernel(ob, (const void *)k_rows_A<T, W>, rgrid, block, a_rows_a, &x, 1);
                 x = gb.add_kernel(ob, (const void *)k_update_S<T, B, W>, grid, block, a_body, &x, 1);
+                if (p.rowpar) x = gb.add_kernel(ob, (const void *)k_rows_B<T, W>, rgrid, block, a_body, &x, 1);
                 cudaGraph_t ib = nullptr;
                 x = gb.add_while(ob, p_body.h_inner, &x, 1, &ib);
                 if (!gb.rc) inner_body(ib, a_body, a_fbody);
                 gb.add_kernel(ob, (const void *)k_rho<T, B, W>, grid_a, block, a_body_rho, &x, 1);
             } else {
                 cudaGraphNode_t x = gb.add_kernel(ob, (const void *)k_outer<T, B, W, false>, grid, block, a_body, nullptr, 0);
-                gb.add_kernel(ob, (const void *)k_update_sI<T, B, W>, grid, block, a_body, &x, 1);
+                if (p.rowpar) x = gb.add_kernel(ob, (const void *)k_rows_A<T, W>, rgrid, block, a_rows_a, &x, 1);
+                x = gb.add_kernel(ob, (const void *)k_update_sI<T, B, W>, grid, block, a_body, &x, 1);
+                if (p.rowpar) gb.add_kernel(ob, (const void *)k_rows_B<T, W>, rgrid, block, a_body, &x, 1);
             }
         }
         void *a_out[] = {&p};

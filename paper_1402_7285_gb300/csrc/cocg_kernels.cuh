@@ -140,6 +140,15 @@ struct Panel {
     c64 *xs, *ps;    // [W][max_col_ent][nz]
     c64 *xq;         // gsQMR: the QMR-smoothed iterates, same layout (null for gsCOCG)
     int32_t qmr;     // 1: gsQMR (results and stopping test from the smoothed iterates)
+    // many kept rows (full-vector shifted solutions): the pair steps leave their
+    // per-pair coefficients here and k_rows_A / k_rows_B apply them over every
+    // (column, kept row, shift), shifts fastest
+    int32_t rowpar;
+    c64 *coefA;      // [W][nz][2]: 1/pi_n, beta^m_{n-1} (p^m update)
+    c64 *coefB;      // [W][nz]: alpha^m_n (x^m update)
+    double *etaA;    // [W][nz]: QMR smoothing weight
+    int32_t *flagA;  // [W][nz]: bit 0 p^m update, bit 1 smoothing update
+    int32_t *flagB;  // [W][nz]: x^m update
     // the column queue (device): columns are loaded into slots in this order
     const int64_t *col_row;     // [n_cols]   right-hand side row j of each column
     const int64_t *col_ptr;     // [n_cols+1] kept-row offsets (rows of G) of each column
