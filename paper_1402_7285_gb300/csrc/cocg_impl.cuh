@@ -794,13 +794,16 @@ __global__ void __launch_bounds__(NT, ctas_light<T, B>()) k_inner_a(Panel<T> p) 
     ld.lane = lane;
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) ld.s[cc] = (X)p.col[lane * CPT + cc].in_beta;
+    // neighbour blocks per trip: one for FP32 vectors, whose operand (t + beta d)
+    // takes two loads per neighbour row (measured faster than two blocks per trip)
+    constexpr int UNR = std::is_same<T, float>::value ? 1 : 2;
     Acc<T> acc[CPT][1];
 #pragma unroll
     for (int cc = 0; cc < CPT; ++cc) acc[cc][0].zero();
     const int64_t br_step = (int64_t)gridDim.x * TM::PER_CTA; // groups dealt round-robin
     for (int64_t br = (int64_t)blockIdx.x * TM::PER_CTA + team; br < p.n_brows; br += br_step) {
         cpx<T> sd[B][CPT];
-        bsr_row_product<T, B, X>(p.s_rp, p.s_ci, p.s_val, br, ld, sd, p.s_unit ? br : -1);
+        bsr_row_product<T, B, X, UNR>(p.s_rp, p.s_ci, p.s_val, br, ld, sd, p.s_unit ? br : -1);
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int64_t row = br * B + i;

@@ -297,29 +297,59 @@ __device__ __forceinline__ void warp_reduce(Acc<float> &s) {
     }
 }
 
-// In the last CTA: out[q] = sum over CTAs of part[q][*] for q < W*K, one warp per q.
+// Lane-group sum over R consecutive lanes (R a power of two <= 32), in a fixed order.
+__device__ __forceinline__ void group_reduce(Acc<double> &s, int R) {
+    for (int o = R / 2; o > 0; o >>= 1) s.s += __shfl_xor_sync(TB_FULL_MASK, s.s, o);
+}
+template <typename A>
+__device__ __forceinline__ void group_reduce(A &s, int R) {
+    for (int o = R / 2; o > 0; o >>= 1) {
+        A t;
+        t.hi = __shfl_xor_sync(TB_FULL_MASK, s.hi, o);
+        t.lo = __shfl_xor_sync(TB_FULL_MASK, s.lo, o);
+        s.add(t);
+    }
+}
+
+// In the last CTA: out[q] = sum over CTAs of part[q][*] for q < W*K.  The
+// last CTA runs alone, so what counts is how many L2 round trips it waits for:
+// RG = NT / (W*K) threads (rounded down to a power of two, at most 32) share a
+// row, each keeps RED_U independent loads in flight, and the RG sums of a row
+// are combined by shuffles.  The order of the additions depends only on the
+// grid and the template arguments, so the sums are reproducible.
 template <typename T, int W, int NT, int K>
 __device__ __forceinline__ void reduce_partials(const void *part, double *out) {
     typedef typename Acc<T>::P P;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr int ROWS = W * K;
+    constexpr int FIT = NT / ROWS >= 32 ? 32 : (NT / ROWS >= 1 ? NT / ROWS : 1);
+    constexpr int RG = FIT >= 16 ? (FIT >= 32 ? 32 : 16) : (FIT >= 8 ? 8 : (FIT >= 4 ? 4 : (FIT >= 2 ? 2 : 1)));
+    constexpr int PASS = NT / RG; // rows per pass
+    constexpr int RED_U = 16;
     const P *pp = reinterpret_cast<const P *>(part);
     const int G = (int)gridDim.x;
-    for (int q = warp; q < W * K; q += NT / 32) {
-        const P *row = pp + (int64_t)q * G;
+    Acc<T> z;
+    z.zero();
+    const P zp = z.pack();
+    const int sub = threadIdx.x % RG;
+    for (int q0 = 0; q0 < ROWS; q0 += PASS) {
+        const int q = q0 + (int)threadIdx.x / RG;
         Acc<T> s;
         s.zero();
-        int t = lane;
-        // four independent loads in flight per lane (the last CTA runs alone)
-        for (; t + 96 < G; t += 128) {
-            const P a = __ldcg(row + t), b = __ldcg(row + t + 32), c = __ldcg(row + t + 64), d = __ldcg(row + t + 96);
-            s.add(Acc<T>::unpack(a));
-            s.add(Acc<T>::unpack(b));
-            s.add(Acc<T>::unpack(c));
-            s.add(Acc<T>::unpack(d));
+        if (q < ROWS) {
+            const P *row = pp + (int64_t)q * G;
+            for (int b0 = sub; b0 < G; b0 += RG * RED_U) {
+                P v[RED_U];
+#pragma unroll
+                for (int u = 0; u < RED_U; ++u) {
+                    const int b = b0 + u * RG;
+                    v[u] = b < G ? __ldcg(row + b) : zp;
+                }
+#pragma unroll
+                for (int u = 0; u < RED_U; ++u) s.add(Acc<T>::unpack(v[u]));
+            }
         }
-        for (; t < G; t += 32) s.add(Acc<T>::unpack(__ldcg(row + t)));
-        warp_reduce(s);
-        if (lane == 0) out[q] = s.value();
+        group_reduce(s, RG);
+        if (sub == 0 && q < ROWS) out[q] = s.value();
     }
     __syncthreads();
 }

@@ -99,7 +99,7 @@ __device__ __forceinline__ void ld_block(const T *__restrict__ blk, T (&a)[B * B
 // the identity (an overlap matrix of orthonormal on-site orbitals): its
 // products are replaced by additions of the operand, which gives the same bits
 // (products with 1 and 0 are exact, and adding an exact zero changes nothing).
-template <typename T, int B, typename X = T, class Loader>
+template <typename T, int B, typename X = T, int UNR = 2, class Loader>
 __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                 const T *__restrict__ val, int64_t br, Loader &ld,
                                                 cpx<T> (&acc)[B][PanelVec<T>::CPT], int64_t unit_row = -1) {
@@ -146,9 +146,10 @@ __device__ __forceinline__ void bsr_row_product(const int64_t *__restrict__ rp, 
         for (int i = 0; i < B; ++i)
 #pragma unroll
             for (int c = 0; c < CPT; ++c) acc[i][c] = mk<T>(0, 0);
-        // two blocks per trip keep twice the neighbour loads in flight (small blocks)
+        // two blocks per trip keep twice the neighbour loads in flight (small
+        // blocks; UNR sets it, 1 where registers are short)
         int64_t col_n = k0 < k1 ? (int64_t)__ldg(ci + k0) : 0;
-#pragma unroll(B <= 4 ? 2 : 1)
+#pragma unroll(B <= 4 ? UNR : 1)
         for (int64_t k = k0; k < k1; ++k) {
             const int64_t col = col_n;
             if (k + 1 < k1) col_n = __ldg(ci + k + 1);

@@ -56,3 +56,18 @@ def test_df_ops_outer_and_streaming_kernels_by_hand():
 
 def test_fp32_peak_is_the_lane_count_times_the_clock():
     assert bench.FP32_PEAK_OPS == 152 * 128 * 2.07e9
+
+
+def test_algorithmic_bytes_df64_refinement():
+    """The df inner solve by refinement: FP32 sweeps on FP32 vectors and FP32
+    values of S, and refinement passes that update the df solution and residual."""
+    V = M * W * 2 * 8
+    V32 = M * W * 2 * 4
+    idx = NNZB * 4 + (NBR + 1) * 8
+    Mb, Mb32 = NNZB * B * B * 8 + idx, NNZB * B * B * 4 + idx
+    got = bench.algorithmic_bytes(M, NNZB, B, NBR, W, NZ, NENT, 8, 4, refine=True)
+    assert got["IC_A_inner_S_product"] == 4 * V32 + Mb32         # T, D_old in; D, A out
+    assert got["IC_B_inner_update"] == 6 * V32                   # C, T rw; D, A in
+    assert got["R_refine"] == 4 * V + 2 * V32 + Mb               # Y, T rw (df); C in, T32 out
+    assert got["R_refine_fp32"] == 4 * V + 2 * V32 + Mb32
+    assert got["B_update"] == 6 * V + V32 + Mb + 3 * NENT * NZ * 16
