@@ -683,7 +683,7 @@ def main():
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
                     help="skip timing one panel with the plain FP64 solver")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--profile-reps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
