@@ -453,14 +453,19 @@ def run_ours(args, rank, world):
         e2e = {"value": e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d_b // e2e_steps,
                "d2h_bytes_per_step": d2h_b // e2e_steps, "steps": e2e_steps}
 
-    # ---- the plain FP64 solver on the same panel (the comparison the metric names)
+    # ---- the plain FP64 solver on the first timed panel's first 32 columns, panel of 32
+    # (the comparison the metric names; FP64 is ALU-bound, so a wider panel would only
+    # lengthen the run)
     fp64 = None
     if args.fp64_compare and prec != tb.TB_PREC_FP64:
-        cols, ptr, orows = panels[0]
+        W64 = min(W, 32)
+        c64 = panel(order[0])[0][:W64]
+        p64_ptr, p64_rows = block_pattern_rows(Hh.row_ptr, Hh.col_idx, Hh.bdim, c64)
+        cols, ptr, orows = (torch.as_tensor(a, device=dev) for a in (c64, p64_ptr, p64_rows))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r64 = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=tb.TB_PREC_FP64, panel_w=W,
+        r64 = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=tb.TB_PREC_FP64, panel_w=W64,
                        max_iter=args.max_iter, ctas_per_sm=args.ctas_per_sm)
         tb.reduce_ldos_dm(ctx, r64.G, zt, wt, mu, kT, cols, ptr, orows, S=S)
         e1.record(stream)
@@ -469,7 +474,8 @@ def run_ours(args, rank, world):
         p64 = converged_pairs(r64)
         fp64 = {"value": p64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64, "steps": 1,
                 "outer_iters": r64.outer_iters, "inner_iters": r64.inner_iters,
-                "note": "same panel as the first timed step, plain FP64 vectors and products"}
+                "columns": int(W64), "panel_w": int(W64),
+                "note": "the first timed step's first columns, plain FP64 vectors and products"}
 
     # ---- roofline of the dominant kernel (CUDA events on this stream)
     cols, ptr, orows = panels[0]
@@ -661,10 +667,10 @@ def cpu_oracle_sample(target_seconds: float, iters_needed: float | None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--panel-w", type=int, default=32)
+    ap.add_argument("--panel-w", type=int, default=64)
     ap.add_argument("--columns-per-step", type=int, default=0,
                     help="columns each step solves through the panel's slots (default: one panel width)")
     ap.add_argument("--precision", default="df64", choices=["df64", "mixed", "fp64"])

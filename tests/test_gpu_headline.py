@@ -2,13 +2,13 @@
 
 The generalized (S != I) system on the 32^3 periodic simple cubic lattice
 (M = 131072, 4x4 blocks), 64 shifts E + 0.005i on [-10, 6], panel 0 of the
-right-hand sides (32 columns of orbital 0 of the 16^3 sub-block), solved
-exactly as the benchmark's step solves it: df64, panel of 32, tolerance 1e-5
+right-hand sides (64 columns of orbital 0 of the 16^3 sub-block), solved
+exactly as the benchmark's step solves it: df64, panel of 64, tolerance 1e-5
 on every shift's relative residual, default inner solve and restart rule,
 then reduced to LDOS and density-matrix elements (midpoint weights,
 chemical potential -2, kT = 0).
 
-Four of its columns are compared with stored results the CPU oracle alone
+Four of its first 32 columns are compared with stored results the CPU oracle alone
 wrote (tests/golden/make_c2_panel_goldens.py): its plain FP64 shifted COCG at
 the same tolerance, and at 1e-9.  Relative errors, per output:
   G     per (column, shift): max over kept rows |dG| / max |G_ref|;
@@ -31,7 +31,7 @@ import workloads as wl
 
 DEV = "cuda:0"
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_panel0_goldens.npz")
-PANEL_W = 32
+PANEL_W = 64
 
 
 def _errors(G, L, D, ptr, rG, rL, rD, rptr):
