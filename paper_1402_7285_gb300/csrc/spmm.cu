@@ -93,12 +93,15 @@ struct SpmmLaunch {
     const void *X;
     void *Y;
     cudaStream_t s;
-    int grid;
+    int sms;
     template <typename T, int B, int W>
     void run() {
         constexpr int NT = 256;
         using TM = Teams<T, W, NT>;
         int64_t need = (n_brows + TM::PER_CTA - 1) / TM::PER_CTA;
+        // FP32: one wave of the four resident CTAs per SM (measured 8 % faster on
+        // C2 than two waves); FP64 and df: eight CTAs per SM
+        const int64_t grid = (int64_t)sms * (std::is_same<T, float>::value ? 4 : 8);
         int g = (int)(need < grid ? need : grid);
         if (g < 1) g = 1;
         if constexpr (std::is_same<T, float>::value)
@@ -107,6 +110,16 @@ struct SpmmLaunch {
             k_spmm<T, B, W, NT><<<g, NT, 0, s>>>(rp, ci, (const T *)val, n_brows, (const T *)X, (T *)Y);
     }
 };
+
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    }
+    return sms;
+}
 
 } // namespace
 
@@ -173,7 +186,7 @@ extern "C" int tb_bsr_spmm(tb_ctx *ctx, const tb_bsr *A, const double *X, int32_
         k_pad_in<df><<<g, 256, 0, s>>>((const double *)x, ncols, (df *)(ws + off_x), W, n);
     else
         k_pad_in<double><<<g, 256, 0, s>>>((const double *)x, ncols, (double *)(ws + off_x), W, n);
-    SpmmLaunch L{(const int64_t *)rp, (const int32_t *)ci, mval, A->n_brows, ws + off_x, ws + off_y, s, 152 * 8};
+    SpmmLaunch L{(const int64_t *)rp, (const int32_t *)ci, mval, A->n_brows, ws + off_x, ws + off_y, s, sm_count()};
     const bool ok = f32 ? dispatch_bw<float>(L, A->bdim, W) : dfp ? dispatch_bw<df>(L, A->bdim, W)
                                                              : dispatch_bw<double>(L, A->bdim, W);
     if (!ok) return set_error(ctx, TB_ERR_UNSUPPORTED, "no SpMM variant");
@@ -234,7 +247,7 @@ extern "C" int tb_bsr_spmm_profile(tb_ctx *ctx, const tb_bsr *A, int32_t ncols, 
         k_fill_panel<df><<<g, 256, 0, s>>>((df *)(ws + off_x), 2 * n * W);
     else
         k_fill_panel<double><<<g, 256, 0, s>>>((double *)(ws + off_x), 2 * n * W);
-    SpmmLaunch L{(const int64_t *)rp, (const int32_t *)ci, mval, A->n_brows, ws + off_x, ws + off_y, s, 152 * 8};
+    SpmmLaunch L{(const int64_t *)rp, (const int32_t *)ci, mval, A->n_brows, ws + off_x, ws + off_y, s, sm_count()};
     auto launch = [&]() {
         return f32 ? dispatch_bw<float>(L, A->bdim, W) : dfp ? dispatch_bw<df>(L, A->bdim, W)
                                                          : dispatch_bw<double>(L, A->bdim, W);
