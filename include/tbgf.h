@@ -189,8 +189,8 @@ typedef struct {
     int32_t inner_max;   /* S != I: inner iterations per outer iteration (DF64: per
                             FP32 sweep), 0 = 40                                   */
     int32_t ctas_per_sm; /* resident CTAs per SM for the panel kernels, 0 = 3;
-                            with df panels and block edges <= 4 the inner S
-                            product and the rho kernel run one more (at most 4) */
+                            the FP32 sweep update of the DF64 refinement runs
+                            one fewer (at least 1)                              */
     void *stream;        /* cudaStream_t to queue work on                         */
     int32_t solver;      /* TB_SOLVER_COCG (default) or TB_SOLVER_QMR                */
     int64_t *stats;      /* optional host array [4]: outer iterations, inner

@@ -1184,6 +1184,7 @@ struct SolveLaunch {
     Panel<double> pd; // type-erased panel (all T-dependent members are pointers)
     int ncta_a = 0;   // grid of IC_A and C (0: ncta): they fit one more CTA per SM than the others
     int ncta_f = 0;   // grid of the FP32 sweep kernels of the refinement (df panels with S)
+    int ncta_fb = 0;  // grid of the FP32 sweep update IC_B (0: ncta_f)
     int rc = TB_OK;
 
     int vec_grid(int W) const {
@@ -1228,7 +1229,8 @@ struct SolveLaunch {
     template <typename T, int B, int W>
     void profile(Panel<T> p) {
         p.in_graph = 0;
-        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta), grid_f(ncta_f > 0 ? ncta_f : ncta);
+        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta), grid_f(ncta_f > 0 ? ncta_f : ncta),
+                   grid_fb(ncta_fb > 0 ? ncta_fb : (ncta_f > 0 ? ncta_f : ncta));
         const int has_s_i = has_s ? 1 : 0;
         const bool ir = p.ir != 0;
         Panel<float> pf = fp32_view(p);
@@ -1240,7 +1242,7 @@ struct SolveLaunch {
         };
         auto inner_b = [&]() {
             if constexpr (std::is_same<T, df>::value)
-                if (ir) return (void)k_inner_b<float, B, W><<<grid_f, block, 0, stream>>>(pf);
+                if (ir) return (void)k_inner_b<float, B, W><<<grid_fb, block, 0, stream>>>(pf);
             k_inner_b<T, B, W><<<grid, block, 0, stream>>>(p);
         };
         // a refinement pass with its work done (outside the graph nothing sets
@@ -1331,7 +1333,8 @@ struct SolveLaunch {
         }
         p.h_outer = gb.handle(g, 1u, cudaGraphCondAssignDefault);
         cudaGraphConditionalHandle h_inner_init = has_s ? gb.handle(g, 0u, 0u) : 0;
-        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta), grid_f(ncta_f > 0 ? ncta_f : ncta);
+        const dim3 grid(ncta), block(NT), grid_a(ncta_a > 0 ? ncta_a : ncta), grid_f(ncta_f > 0 ? ncta_f : ncta),
+                   grid_fb(ncta_fb > 0 ? ncta_fb : (ncta_f > 0 ? ncta_f : ncta));
         const bool ir = p.ir != 0;
         int has_s_i = has_s ? 1 : 0;
         int init1 = 1, init0 = 0;
@@ -1353,7 +1356,7 @@ struct SolveLaunch {
             if constexpr (std::is_same<T, df>::value) {
                 if (ir) {
                     cudaGraphNode_t y = gb.add_kernel(ib, (const void *)k_inner_a<float, B, W>, grid_f, block, a_f, nullptr, 0);
-                    y = gb.add_kernel(ib, (const void *)k_inner_b<float, B, W>, grid_f, block, a_f, &y, 1);
+                    y = gb.add_kernel(ib, (const void *)k_inner_b<float, B, W>, grid_fb, block, a_f, &y, 1);
                     gb.add_kernel(ib, (const void *)k_refine<T, B, W>, grid, block, a_t, &y, 1);
                     return;
                 }
