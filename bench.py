@@ -431,7 +431,7 @@ def run_ours(args, rank, world):
         Sp = tb.Bsr(Sh.n_brows, Sh.bdim, pin(Sh.row_ptr), pin(Sh.col_idx), pin(Sh.val))
         zp = pin(z)
         wp = pin(w_q)
-        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        e2e_steps = max(1, min(len(order), args.e2e_steps))   # panels 0, 1, ... (any panel of the workload)
         host_panels = [tuple(pin(a) for a in panel(order[s])) for s in range(e2e_steps)]
         h2d = sum(int(a.numel() * a.element_size()) for a in (Hp.row_ptr, Hp.col_idx, Hp.val, Sp.row_ptr,
                                                              Sp.col_idx, Sp.val, zp, wp))

@@ -134,7 +134,9 @@ def test_learned_order_gains_over_plain_order(ctx):
     plain = scheduler.greedy_makespan(cost, np.arange(len(cost)), workers)
     learned = scheduler.greedy_makespan(cost, scheduler.longest_first(p_it * size), workers)
     best = scheduler.greedy_makespan(cost, scheduler.longest_first(cost), workers)
-    assert learned <= plain
+    # measured: modeled makespan gain 1.096 (equal to the exact order), rank correlation 0.997
+    assert learned <= 0.98 * plain, (learned, plain)
+    assert learned <= 1.02 * best, (learned, best)
     print(f"makespan plain {plain:.3e} learned {learned:.3e} exact-order {best:.3e} "
           f"(gain {plain / learned:.3f}); rank corr {rho:.3f}")
     # the same comparison on the GPU: solve the held-out columns in both orders
@@ -152,4 +154,5 @@ def test_learned_order_gains_over_plain_order(ctx):
         times[name] = time.perf_counter() - t0
         assert np.array_equal(_np(r.iters), true_it.astype(np.int32))
     print(f"GPU time plain {times['plain']:.3f}s learned {times['learned']:.3f}s")
-    assert times["learned"] <= 1.05 * times["plain"]
+    # measured: 0.417 s against 0.636 s (1.53x)
+    assert times["learned"] <= 0.9 * times["plain"], times
