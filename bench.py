@@ -458,14 +458,14 @@ def run_ours(args, rank, world):
     # lengthen the run)
     fp64 = None
     if args.fp64_compare and prec != tb.TB_PREC_FP64:
-        W64 = min(W, 32)
-        c64 = panel(order[0])[0][:W64]
-        p64_ptr, p64_rows = block_pattern_rows(Hh.row_ptr, Hh.col_idx, Hh.bdim, c64)
-        cols, ptr, orows = (torch.as_tensor(a, device=dev) for a in (c64, p64_ptr, p64_rows))
+        w_fp64 = min(W, 32)
+        cols_fp64 = panel(order[0])[0][:w_fp64]
+        p64_ptr, p64_rows = block_pattern_rows(Hh.row_ptr, Hh.col_idx, Hh.bdim, cols_fp64)
+        cols, ptr, orows = (torch.as_tensor(a, device=dev) for a in (cols_fp64, p64_ptr, p64_rows))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r64 = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=tb.TB_PREC_FP64, panel_w=W64,
+        r64 = tb.solve(ctx, H, S, zt, cols, ptr, orows, tol=WORKLOAD.tol, precision=tb.TB_PREC_FP64, panel_w=w_fp64,
                        max_iter=args.max_iter, ctas_per_sm=args.ctas_per_sm)
         tb.reduce_ldos_dm(ctx, r64.G, zt, wt, mu, kT, cols, ptr, orows, S=S)
         e1.record(stream)
@@ -474,7 +474,7 @@ def run_ours(args, rank, world):
         p64 = converged_pairs(r64)
         fp64 = {"value": p64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64, "steps": 1,
                 "outer_iters": r64.outer_iters, "inner_iters": r64.inner_iters,
-                "columns": int(W64), "panel_w": int(W64),
+                "columns": int(w_fp64), "panel_w": int(w_fp64),
                 "note": "the first timed step's first columns, plain FP64 vectors and products"}
 
     # ---- roofline of the dominant kernel (CUDA events on this stream)
